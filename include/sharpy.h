@@ -1,0 +1,226 @@
+/*
+ * sharpy — GPU hot path of a Sequential Monte Carlo sampler with a No-U-Turn
+ * transition kernel for gravitational-wave inference (arXiv:2601.02336,
+ * "The Sequential Monte Carlo goes NUTS").
+ *
+ * C ABI. Plain pointers and sizes; no C++ or torch types. Every call returns
+ * an int status (SHARPY_OK = 0, negative on error), never aborts, never
+ * throws, and never synchronises the device except where stated
+ * (sharpy_set_data, sharpy_log_evidence, sharpy_get_status, sharpy_smc_run).
+ *
+ * Memory: arrays are FP64, row-major and contiguous unless stated. Device
+ * pointers are owned by the caller and must stay valid until the work queued
+ * on `stream` has finished. Tables, scratch and the status word are owned by
+ * the context. A context is bound to one device and may be used from one
+ * host thread at a time. Calls on one context are stream-ordered; running
+ * calls of one context concurrently on different streams is not supported
+ * (they share the context's scratch).
+ *
+ * Parameters theta are the free dimensions of the model ([N][D], D =
+ * cfg->n_dim); the physical meaning of dimension i is cfg->phys[i]. Units:
+ * chirp mass [Msun], distance [Mpc], times [s], angles [rad].
+ */
+#ifndef SHARPY_H
+#define SHARPY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sharpy_ctx sharpy_ctx;
+/* A cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* sharpy_stream;
+
+enum {
+  SHARPY_OK = 0,
+  SHARPY_EINVAL = -1,     /* bad argument (null pointer, size, range)          */
+  SHARPY_ECUDA = -2,      /* a CUDA runtime call failed                        */
+  SHARPY_ENOMEM = -3,     /* device or host allocation failed                  */
+  SHARPY_ENONFINITE = -4, /* NaN/Inf in data or PSD, or a non-finite ln L       */
+  SHARPY_ETIMEOUT = -5,   /* a device loop hit its iteration bound             */
+  SHARPY_EBOUNDS = -6,    /* a device index check failed                       */
+  SHARPY_ESTATE = -7      /* call out of order (e.g. no data set yet)          */
+};
+
+/* Arithmetic of the likelihood sweep. */
+enum {
+  SHARPY_FP64 = 0,  /* every per-bin operation in FP64                                     */
+  SHARPY_MIXED = 1, /* FP64 phase, FP32 carrier and inner products, FP64 reductions/epilogue */
+  SHARPY_MIXED_SPLIT = 2 /* phase in split single precision (no FP64 in the bin loop), FP32 rest */
+};
+
+/* Models. */
+enum {
+  SHARPY_MODEL_TAYLORF2 = 0, /* Whittle likelihood of a TaylorF2 signal (Sec. 2, Eq. 2) */
+  SHARPY_MODEL_GAUSSMIX = 1  /* diagonal Gaussian mixture ln L (test targets, App. A)     */
+};
+
+/* Physical parameters of the aligned-spin TaylorF2 model. */
+enum {
+  SHARPY_MC = 0, SHARPY_Q = 1, SHARPY_CHI1 = 2, SHARPY_CHI2 = 3, SHARPY_DL = 4, SHARPY_COSI = 5,
+  SHARPY_PHIC = 6, SHARPY_PSI = 7, SHARPY_RA = 8, SHARPY_SINDEC = 9, SHARPY_TC = 10,
+  SHARPY_NPHYS = 11
+};
+
+enum { SHARPY_PRIOR_UNIFORM = 0, SHARPY_PRIOR_POWER2 = 1 }; /* density ~ const or ~ x^2 on [lo,hi] */
+enum { SHARPY_BOUND_REFLECT = 0, SHARPY_BOUND_PERIODIC = 1 }; /* Sec. 5, "Boundary conditions" */
+
+#define SHARPY_MAX_DIM 11
+#define SHARPY_MAX_COMP 4
+#define SHARPY_MAX_DET 4
+#define SHARPY_MAX_DEPTH 10
+
+/* Model and prior (Sec. 2 Eq. 1; Sec. 5). */
+typedef struct {
+  int model;                        /* SHARPY_MODEL_*                                   */
+  int n_dim;                        /* D, 1..11                                          */
+  int phys[SHARPY_MAX_DIM];         /* TaylorF2: physical parameter of free dimension i  */
+  double lo[SHARPY_MAX_DIM];        /* prior box [lo, hi]                                */
+  double hi[SHARPY_MAX_DIM];
+  int prior[SHARPY_MAX_DIM];        /* SHARPY_PRIOR_*                                    */
+  int boundary[SHARPY_MAX_DIM];     /* SHARPY_BOUND_*                                    */
+  double fixed[SHARPY_NPHYS];       /* TaylorF2: values of the parameters that are not free */
+  int n_comp;                       /* GAUSSMIX: ln L = log sum_c exp(logw_c) N(x; mu_c, diag sigma_c^2) */
+  double mix_logw[SHARPY_MAX_COMP];
+  double mix_mu[SHARPY_MAX_COMP][SHARPY_MAX_DIM];
+  double mix_sigma[SHARPY_MAX_COMP][SHARPY_MAX_DIM];
+} sharpy_config;
+
+/* Detector on a spherical Earth (GMST = 0). Arms at `azimuth` (clockwise from
+   local north) and azimuth + pi/2. fixed_response = 1 uses fplus, fcross and
+   delay as given, independent of the sky position and polarisation. */
+typedef struct {
+  double lat, lon, azimuth;
+  int fixed_response;
+  double fplus, fcross, delay;
+} sharpy_detector;
+
+/* Per-particle NUTS statistics, accumulated over the n_steps transitions of
+   one sharpy_nuts_mutate call. */
+typedef struct {
+  double accept_sum;  /* sum of per-transition mean min(1, exp(-dH))              */
+  double active_bins; /* sum over gradient evaluations of the bins below f_ISCO x detectors */
+  int depth_sum;      /* sum of tree depths                                         */
+  int n_leapfrog;     /* leapfrog steps = likelihood+gradient evaluations           */
+  int n_divergent;    /* transitions that stopped on a divergence (dH > 1000)       */
+  int pad;
+} sharpy_nuts_stats;
+
+/* Full-run options (Sec. 3 and Sec. 6 run settings). */
+typedef struct {
+  int64_t n_particles;
+  double alpha;        /* target ESS fraction, Eq. (6)                               */
+  int n_mut;           /* NUTS transitions per stage                                 */
+  int max_depth;       /* NUTS tree depth limit (<= SHARPY_MAX_DEPTH)                */
+  int metric;          /* 0: identity, step = eps_scale * min_j sigma_j; 1: weighted covariance, step = eps_scale */
+  double eps_scale;
+  int precision;       /* SHARPY_FP64 / SHARPY_MIXED / SHARPY_MIXED_SPLIT            */
+  int max_stages;
+} sharpy_smc_options;
+
+typedef struct {
+  double beta, dbeta, ess, dlnz, eps, accept_mean, depth_mean;
+  int64_t n_leapfrog;
+  int n_divergent;
+  int pad;
+  double active_bins;
+} sharpy_stage;
+
+/* Context. Owns the staged data tables, scratch, the evidence accumulator and
+   the sticky status word. cfg is copied. Returns SHARPY_EINVAL for an invalid
+   configuration, SHARPY_ECUDA / SHARPY_ENOMEM on device errors. */
+int sharpy_create(sharpy_ctx** out, const sharpy_config* cfg, int device);
+void sharpy_destroy(sharpy_ctx* ctx);
+
+/* Stage one event (Sec. 2, Eq. 2): frequency grid f_k = f_min + k df,
+   k < n_bins; data d[n_det][n_bins][2] (re, im) and one-sided PSD
+   psd[n_det][n_bins], both HOST arrays, copied (the caller keeps ownership).
+   Builds the noise weights w = 4 df / S, the pre-whitened data, the basis and
+   prefix tables and <d|d>. Synchronous. SHARPY_ENONFINITE if d or the PSD has
+   a NaN/Inf or the PSD is not positive. */
+int sharpy_set_data(sharpy_ctx* ctx, int n_det, int64_t n_bins, double f_min, double df,
+                    const double* d_re_im, const double* psd, const sharpy_detector* det);
+
+/* Prior draws (Philox4x32-10, purpose 1, counter (particle, ctr, 1, dim)). theta: [N][D] device. */
+int sharpy_prior_sample(sharpy_ctx* ctx, int64_t n, double* theta, uint64_t key, uint64_t ctr,
+                        sharpy_stream stream);
+/* ln pi(theta) [N] and grad ln pi [N][D] (glp may be NULL); device arrays.
+   Outside the box ln pi = -inf. */
+int sharpy_prior_logpdf_grad(sharpy_ctx* ctx, int64_t n, const double* theta, double* lp, double* glp,
+                             sharpy_stream stream);
+
+/* Whittle log-likelihood ln L = -1/2 <d-h|d-h> (Sec. 2, Eq. 2) and its
+   gradient (Sec. 4: exact derivative, here a hand-written adjoint over
+   per-bin moments) at N parameter vectors. theta [N][D], lnl [N],
+   grad [N][D] or NULL (forward-only sweep): device arrays. precision:
+   SHARPY_FP64 / SHARPY_MIXED / SHARPY_MIXED_SPLIT. Asynchronous. */
+int sharpy_loglike_grad(sharpy_ctx* ctx, int64_t n, const double* theta, double* lnl, double* grad,
+                        int precision, sharpy_stream stream);
+
+/* Detector-frame strain h_a(f_k) [N][n_det][n_bins][2] (device) of N
+   parameter vectors (used to build injections). FP64. TaylorF2 only. */
+int sharpy_waveform(sharpy_ctx* ctx, int64_t n, const double* theta, double* h, sharpy_stream stream);
+
+/* n_steps multinomial NUTS transitions per particle (Sec. 4; Hoffman &
+   Gelman 2014) targeting L^beta * pi (Sec. 3, Eq. 3), leapfrog per Sec. 4
+   Eqs. (11)-(13), boundary maps per Sec. 5. theta, lnl, grad (grad ln L)
+   are updated in place (device). inv_mass: [D][D] device metric, or NULL
+   for the identity. step: leapfrog step. max_depth <= SHARPY_MAX_DEPTH.
+   Random numbers: Philox4x32-10 keyed by `key`, transition t of particle i
+   uses step counter ctr + t. stats: [N] device or NULL. One persistent
+   launch; uneven trees are handled on the device. */
+int sharpy_nuts_mutate(sharpy_ctx* ctx, int64_t n, double beta, double* theta, double* lnl,
+                       double* grad, const double* inv_mass, double step, int max_depth, int n_steps,
+                       uint64_t key, uint64_t ctr, int precision, sharpy_nuts_stats* stats,
+                       sharpy_stream stream);
+
+/* One tempering step (Sec. 3, Eqs. 4-8): the increment dbeta solving
+   ESS = alpha N by 100 bisection steps (or dbeta = 1 - beta_prev if that
+   already keeps ESS >= alpha N), weights W_i = exp(dbeta (lnL_i - max)),
+   dlnz = logsumexp(dbeta lnL) - ln N (also added to the context's ln Z),
+   the weighted covariance of theta under W (cov [D][D], or NULL), then
+   systematic resampling with uniform u in [0,1) (see
+   sharpy_systematic_resample) and the gather of theta, lnl, grad in place.
+   beta_next, dlnz, ess: device scalars; ancestors [N] int32 device or NULL.
+   N <= 1<<20. */
+int sharpy_smc_reweight_resample(sharpy_ctx* ctx, int64_t n, double* theta, double* lnl, double* grad,
+                                 double beta_prev, double alpha, double u, double* beta_next,
+                                 double* dlnz, double* ess, int32_t* ancestors, double* cov,
+                                 sharpy_stream stream);
+
+/* Systematic resampling on integer-quantised weights (bit-exact): W [N] in
+   [0,1] (device), q_i = floor(W_i 2^32), C = inclusive prefix sum,
+   U = floor(u 2^32), p_m = floor((m 2^32 + U) C_{N-1} / (N 2^32)),
+   ancestor(m) = min{ j : C_j > p_m }. anc [N] int32 device. Needs no context.
+   SHARPY_EINVAL if u is outside [0,1) or N is outside [1, 1<<20]. An all-zero
+   W is reported through ancestors = -1. */
+int sharpy_systematic_resample(int64_t n, const double* w, double u, int32_t* anc, sharpy_stream stream);
+
+/* Reset the context's evidence accumulator (ln Z = 0, zero stages). */
+int sharpy_reset_evidence(sharpy_ctx* ctx, sharpy_stream stream);
+/* Sum of the evidence increments since the last reset (Sec. 3.1, Eq. 8) and
+   the number of stages. Synchronises the context's last stream. */
+int sharpy_log_evidence(sharpy_ctx* ctx, double* lnz, int* n_stages);
+
+/* Full SMC run (Sec. 3): prior draw, ln L, then stages of reweight/resample,
+   metric and step size, n_mut NUTS transitions, until beta = 1. The stage
+   loop runs on the device except for one 8-byte read of beta per stage.
+   theta_out [N][D], lnl_out [N]: device or NULL; stages: HOST array of
+   opt->max_stages entries or NULL. Returns SHARPY_ETIMEOUT if beta = 1 was
+   not reached within max_stages. Synchronous. */
+int sharpy_smc_run(sharpy_ctx* ctx, const sharpy_smc_options* opt, uint64_t key, double* lnz,
+                   int* n_stages, double* theta_out, double* lnl_out, sharpy_stage* stages,
+                   sharpy_stream stream);
+
+/* Sticky device status (synchronises): SHARPY_OK or the first error a kernel
+   recorded. sharpy_clear_status resets it. */
+int sharpy_get_status(sharpy_ctx* ctx);
+int sharpy_clear_status(sharpy_ctx* ctx);
+const char* sharpy_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

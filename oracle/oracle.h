@@ -1,0 +1,174 @@
+/*
+ * Oracle for the SMC-with-NUTS Whittle-likelihood sampler — TEST
+ * INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, FP64 CPU implementation of what the GPU library computes,
+ * written from the paper's definitions. Only the test suite, the smoke check
+ * and the CPU-baseline leg of the benchmark load it. It shares no code,
+ * header, table or constant with the CUDA library, and the library never
+ * loads it.
+ *
+ * What it follows:
+ *   - Whittle log-likelihood, Sec. 2 Eq. (2): ln L = -1/2 <d-h|d-h>,
+ *     <a|b> = 4 Re sum_k a_k^* b_k / S_k * df  (the literal sum, all bins).
+ *   - Bayes / evidence definitions, Sec. 2 Eq. (1); tempered targets
+ *     L^beta * pi, Sec. 3 Eq. (3); reweighting Eq. (4); ESS Eq. (5);
+ *     adaptive beta Eq. (6); resampling (Sec. 3 item 2); evidence ratios
+ *     Sec. 3.1 Eqs. (7)-(8).
+ *   - Hamiltonian, leapfrog, NUTS: Sec. 4 Eqs. (9)-(13) and the NUTS
+ *     reference cited there (Hoffman & Gelman 2014), multinomial variant.
+ *   - Reflective / periodic boundaries: Sec. 5, "Boundary conditions".
+ *   - Waveform: TaylorF2 (3.5PN non-spinning phase, aligned-spin terms to
+ *     2.5PN, Newtonian amplitude, cut at f_ISCO), the workload's stand-in
+ *     for the paper's IMRPhenomD (Sec. 6).
+ *
+ * Gradients come from forward-mode dual numbers through the literal
+ * per-bin sum (dual.h): exact up to rounding, independent of the GPU
+ * library's moment-based adjoint.
+ *
+ * Parity pins live in tests/ (closed forms, finite differences, analytic
+ * evidences, brute force). Functions without a pin: the physical value of
+ * the self-spin coefficient in sigma ("parity unpinned": only the formula
+ * as written is checked).
+ */
+#ifndef SHARPY_ORACLE_H
+#define SHARPY_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Physical parameters of the aligned-spin model. */
+enum {
+  REF_MC = 0,     /* chirp mass [Msun] */
+  REF_Q = 1,      /* mass ratio m2/m1 in (0, 1] */
+  REF_CHI1 = 2,   /* aligned spin of the heavier body */
+  REF_CHI2 = 3,   /* aligned spin of the lighter body */
+  REF_DL = 4,     /* luminosity distance [Mpc] */
+  REF_COSI = 5,   /* cosine of the inclination */
+  REF_PHIC = 6,   /* coalescence phase [rad] */
+  REF_PSI = 7,    /* polarisation angle [rad] */
+  REF_RA = 8,     /* right ascension [rad] (GMST = 0) */
+  REF_SINDEC = 9, /* sine of the declination */
+  REF_TC = 10,    /* coalescence time [s] */
+  REF_NPHYS = 11
+};
+
+enum { REF_KIND_GW = 0, REF_KIND_GAUSSMIX = 1 };
+enum { REF_PRIOR_UNIFORM = 0, REF_PRIOR_POWER2 = 1 };
+enum { REF_BOUND_REFLECT = 0, REF_BOUND_PERIODIC = 1 };
+
+#define REF_MAX_DIM 11
+#define REF_MAX_COMP 4
+#define REF_MAX_DET 4
+
+typedef struct {
+  int kind;                     /* REF_KIND_* */
+  int n_dim;                    /* D, free dimensions */
+  int phys[REF_MAX_DIM];        /* GW: physical parameter of free dim i */
+  double lo[REF_MAX_DIM];       /* prior box */
+  double hi[REF_MAX_DIM];
+  int prior[REF_MAX_DIM];       /* REF_PRIOR_* */
+  int boundary[REF_MAX_DIM];    /* REF_BOUND_* */
+  double fixed[REF_NPHYS];      /* GW: value of each non-free parameter */
+  /* Gaussian mixture (test targets): ln L = log sum_c w_c N(x; mu_c, diag sigma_c^2) */
+  int n_comp;
+  double mix_logw[REF_MAX_COMP];
+  double mix_mu[REF_MAX_COMP][REF_MAX_DIM];
+  double mix_sigma[REF_MAX_COMP][REF_MAX_DIM];
+} ref_model;
+
+typedef struct {
+  double lat, lon, azimuth;     /* radians; arms at azimuth and azimuth + pi/2 */
+  int fixed_response;           /* 1: use fplus, fcross, delay as given */
+  double fplus, fcross, delay;
+} ref_detector;
+
+typedef struct {
+  int n_det;
+  int64_t n_bins;
+  double f_min, df;             /* f_k = f_min + k * df */
+  const double* data;           /* [n_det][n_bins][2] (re, im) */
+  const double* psd;            /* [n_det][n_bins] one-sided PSD */
+  ref_detector det[REF_MAX_DET];
+} ref_event;
+
+typedef struct {
+  double accept_sum;            /* sum over transitions of the mean min(1, e^{-dH}) */
+  int depth_sum;                /* sum over transitions of the tree depth reached */
+  int n_leapfrog;               /* total leapfrog steps (= likelihood+gradient evaluations) */
+  int n_divergent;              /* transitions that ended on a divergence */
+} ref_nuts_stats;
+
+typedef struct {
+  int64_t n_particles;
+  double alpha;                 /* target ESS fraction */
+  int n_mut;                    /* NUTS transitions per stage */
+  int max_depth;
+  int metric;                   /* 0: identity, eps = eps_scale * min_j sigma_j; 1: dense weighted covariance, eps = eps_scale */
+  double eps_scale;
+  int max_stages;
+} ref_smc_opts;
+
+typedef struct {
+  double beta, dbeta, ess, dlnz, eps, accept_mean, depth_mean;
+  int64_t n_leapfrog;
+  int n_divergent;
+} ref_stage;
+
+/* Philox4x32-10 (Salmon et al., SC'11): 10 rounds, multipliers
+   0xD2511F53 / 0xCD9E8D57, Weyl key increments 0x9E3779B9 / 0xBB67AE85. */
+void ref_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* Two uniforms in (0, 1) with 53-bit resolution from one Philox block. */
+void ref_uniform2(uint64_t key, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, double u[2]);
+/* Two standard normals (Box-Muller) from one Philox block. */
+void ref_normal2(uint64_t key, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, double z[2]);
+
+/* Antenna pattern and geocentric delay of one detector for a source at
+   (ra, sin_dec) with polarisation psi, GMST = 0. */
+void ref_antenna(const ref_detector* det, double ra, double sin_dec, double psi,
+                 double* fplus, double* fcross, double* delay);
+
+/* TaylorF2 pieces, exposed for the closed-form pins. */
+double ref_pn_phase(double mc, double q, double chi1, double chi2, double f);   /* (3/128 eta v^5) sum phi_k v^k */
+double ref_pn_beta(double q, double chi1, double chi2);                          /* 1.5PN spin-orbit beta */
+double ref_amplitude(double mc, double dl, double f);                            /* Newtonian |h~| for an optimal source */
+double ref_f_isco(double mc, double q);
+
+/* Detector-frame strain h_a(f_k) of one parameter vector theta (free dims). */
+int ref_waveform(const ref_model* m, const ref_event* ev, const double* theta, double* h);
+
+/* ln L (and its gradient if grad != NULL) of N parameter vectors [N][D]. */
+int ref_loglike(const ref_model* m, const ref_event* ev, int64_t n, const double* theta,
+                double* lnl, double* grad);
+
+/* Prior: draws (Philox purpose 1), log-density and gradient. */
+int ref_prior_sample(const ref_model* m, int64_t n, double* theta, uint64_t key, uint32_t ctr);
+int ref_prior_logpdf_grad(const ref_model* m, int64_t n, const double* theta, double* lp, double* glp);
+
+/* n_steps NUTS transitions per particle at target L^beta * pi, in place.
+   inv_mass: [D][D] or NULL (identity). stats: [N] or NULL. */
+int ref_nuts_mutate(const ref_model* m, const ref_event* ev, int64_t n, double beta,
+                    double* theta, double* lnl, double* grad, const double* inv_mass,
+                    double step, int max_depth, int n_steps, uint64_t key, uint32_t ctr,
+                    ref_nuts_stats* stats);
+
+/* Adaptive tempering step: beta_next, the incremental weights W (max 1),
+   their ESS and the evidence increment dlnz = logsumexp(dbeta lnL) - ln N. */
+int ref_smc_reweight(int64_t n, const double* lnl, double beta_prev, double alpha,
+                     double* beta_next, double* dlnz, double* ess, double* w);
+/* Systematic resampling on integer-quantised weights (bit-exact). */
+int ref_systematic_resample(int64_t n, const double* w, double u, int32_t* anc);
+/* Weighted mean-centred covariance [D][D]. */
+int ref_weighted_cov(int d, int64_t n, const double* theta, const double* w, double* cov);
+
+/* Full SMC run from the prior to beta = 1. */
+int ref_smc_run(const ref_model* m, const ref_event* ev, const ref_smc_opts* o, uint64_t key,
+                double* lnz, int* n_stages, double* theta_out, double* lnl_out,
+                ref_stage* stages);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
