@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Benchmark of the SMC-NUTS hot path: grad-lnL evaluations per second and
+SMC-NUTS run time, mixed precision vs FP64, on the 11-D aligned-spin TaylorF2
+workload (3 detectors, 8 s at 1/8 Hz, 8033 bins, 2048 particles, NUTS depth 6).
+
+One step = one full SMC run (prior draw, then stages of adaptive reweighting,
+ESS root-find, evidence increment, covariance, systematic resampling and
+gather, and 2 NUTS transitions per particle until beta = 1), i.e. every step
+of the hot path over one synthetic event. value = gradient evaluations (one
+leapfrog of one particle = one ln L + gradient over all detectors and active
+bins) per second, summed over ranks (one independent event per GPU).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sharpy|reference]
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grad-lnL evals/s and SMC-NUTS run time, mixed vs FP64 on GB300, |ΔlnZ|≤2σ"
+UNIT = "evals/s"
+# Algorithmic work per active (bin, detector) of the mixed gradient sweep with 3
+# detectors: FP64 phase = 8 FMA per bin shared by the detectors + 1 FMA per
+# detector; FP32 = angle scale 1, carrier 6, moments 9 x 4 + 2 = 38 -> 45 FLOP.
+FP64_FLOP_PER_BIN_DET = 2.0 * (8.0 / 3.0 + 1.0)
+FP32_FLOP_PER_BIN_DET = 45.0
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _oracle_sample(n_particles, seed):
+    """A bounded sample of the workload for the oracle: one NUTS transition of
+    n_particles particles of the same event at beta = 0.5 (mid-run state)."""
+    import oracle
+    from paper_2601_02336_gb300 import inputs
+    from tests import helpers
+    w = inputs.bbh11()
+    ev, th_inj, _ = helpers.make_event(w, seed=0)
+    model = helpers.oracle_model(w)
+    th = inputs.ball(w, th_inj, n_particles, 500 + seed, rel=1e-3)
+    lnl, g = oracle.loglike(model, ev, th)
+    sig = np.std(th, axis=0)
+    eps = 0.5 * float(np.min(sig))
+    t0 = time.perf_counter()
+    _, _, _, st = oracle.nuts_mutate(model, ev, 0.5, th, lnl, g, None, eps, w.max_depth, 1, key=77 + seed, ctr=1)
+    dt = time.perf_counter() - t0
+    return int(st["n_leapfrog"].sum()), dt
+
+
+def run_reference(args):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    cores = os.cpu_count()
+    n_part = 8 * cores
+    for i in range(args.warmup):
+        _oracle_sample(n_part, i)
+    evals, secs = 0, 0.0
+    for k in range(args.steps):
+        e, dt = _oracle_sample(n_part, 100 + k)
+        evals += e
+        secs += dt
+    v = evals / secs
+    sample = (f"oracle NUTS, one transition of {n_part} particles per step at beta=0.5 near the injection, "
+              f"bbh11 event (8033 bins x 3 detectors), OpenMP over particles")
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": "bbh11 (bounded oracle sample)"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sharpy", choices=["sharpy", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2601_02336_gb300 import api, inputs
+    from paper_2601_02336_gb300._lib import lib
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def allmax(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t[0])
+
+    def allsum(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t[0])
+
+    w = inputs.bbh11()
+    ctx, th_inj, data = api.make_event(w, seed=rank, device=local)
+    run_args = (w.n_particles, w.alpha, w.n_mut, w.max_depth, w.metric, w.eps_scale)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def one_run(key, precision, timing=True):
+        return ctx.smc_run(*run_args, key=key, precision=precision, timing=timing)
+
+    for i in range(args.warmup):
+        one_run(10_000 + 1000 * rank + i, args.precision)
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    evals = 0
+    bins = 0.0
+    nuts_ms = 0.0
+    launches = 0
+    step_ms = []
+    lnzs = []
+    n_stages = []
+    for k in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lnz, th, ll, rec = one_run(20_000 + 1000 * rank + k, args.precision)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        evals += sum(r["n_leapfrog"] for r in rec)
+        bins += sum(r["active_bins"] for r in rec)
+        nuts_ms += sum(r["nuts_ms"] for r in rec)
+        launches += 2 + 5 * len(rec)
+        lnzs.append(lnz)
+        n_stages.append(len(rec))
+    barrier()
+    clk = clocks.stop()
+    t_rank = sum(step_ms)
+    t_max = allmax(t_rank)
+    total_evals = allsum(evals)
+    value = total_evals / (t_max * 1e-3)
+
+    # roofline of the dominant kernel (persistent NUTS), from its in-run durations
+    peaks = (C.c_double * 3)()
+    lib().sharpy_probe_peaks(local, peaks)
+    fp32_peak, fp64_peak = peaks[0], peaks[1]
+    fp64_ach = bins * FP64_FLOP_PER_BIN_DET / (nuts_ms * 1e-3) / 1e12
+    fp32_ach = bins * FP32_FLOP_PER_BIN_DET / (nuts_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "nuts_kernel<MIXED,3>" if args.precision == "mixed" else
+                "nuts_kernel<FP64,3>", "achieved": fp64_ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": fp64_ach / fp64_peak if fp64_peak else None, "traffic": None,
+                "pipe": "fp64 (phase polynomial)", "peak_source": "measured FP64 FMA probe, this GPU",
+                "fp32_achieved": fp32_ach, "fp32_peak": fp32_peak,
+                "fp32_frac": fp32_ach / fp32_peak if fp32_peak else None,
+                "nuts_share_of_step": nuts_ms / t_rank,
+                "active_bin_det_per_eval": bins / max(evals, 1)}
+
+    # the other precision for the mixed-vs-FP64 comparison and |d lnZ| <= 2 sigma
+    other = {}
+    if args.fp64_steps > 0 and args.precision == "mixed":
+        ev_o, t_o, lz_o = 0, 0.0, []
+        for k in range(args.fp64_steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lnz, th, ll, rec = one_run(30_000 + 1000 * rank + k, "fp64")
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_o += e0.elapsed_time(e1)
+            ev_o += sum(r["n_leapfrog"] for r in rec)
+            lz_o.append(lnz)
+        se_m = np.std(lnzs, ddof=1) / math.sqrt(len(lnzs)) if len(lnzs) > 1 else float("nan")
+        se_f = np.std(lz_o, ddof=1) / math.sqrt(len(lz_o)) if len(lz_o) > 1 else float("nan")
+        other = {"fp64_value": ev_o / (t_o * 1e-3), "fp64_ms_per_step": t_o / args.fp64_steps,
+                 "speedup_mixed_over_fp64": value / world / (ev_o / (t_o * 1e-3)),
+                 "lnz_mixed": [float(x) for x in lnzs], "lnz_fp64": [float(x) for x in lz_o],
+                 "dlnz": float(np.mean(lnzs) - np.mean(lz_o)),
+                 "two_sigma": float(2.0 * math.sqrt(se_m ** 2 + se_f ** 2))}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        psd = inputs.psd_array(w)
+        dets = inputs.detectors(w)
+        h_data = torch.from_numpy(np.ascontiguousarray(data)).pin_memory()
+        h_psd = torch.from_numpy(np.ascontiguousarray(psd)).pin_memory()
+        e_evals, e_secs = 0, 0.0
+        K = w.n_bins
+        h2d = K * (8 + 9 * 8 + 9 * 4) + w.n_det * K * (16 + 8 + 8)
+        d2h = 0
+        for k in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.set_data(h_data.numpy(), h_psd.numpy(), w.f_min, w.df, dets)
+            lnz, th, ll, rec = one_run(40_000 + 1000 * rank + k, args.precision, timing=False)
+            th_h = th.cpu()
+            ll_h = ll.cpu()
+            torch.cuda.synchronize()
+            e_secs += time.perf_counter() - t0
+            e_evals += sum(r["n_leapfrog"] for r in rec)
+            d2h = th_h.numel() * 8 + ll_h.numel() * 8 + 8 * (9 * len(rec) + 2)
+        e_max = allmax(e_secs)
+        e2e = {"value": allsum(e_evals) / e_max, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cores = os.cpu_count()
+        n_part = 8 * cores
+        e, dt = _oracle_sample(n_part, 0)
+        cpu = {"value": e / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"oracle NUTS, one transition of {n_part} particles at beta=0.5 near the injection "
+                         f"of the same workload ({e} gradient evaluations, {dt:.1f} s)"}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None,
+               "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+               "config": {"workload": "bbh11: 11-D aligned-spin TaylorF2, 3 detectors, 8 s at 1/8 Hz "
+                                      "(8033 bins, 20-1024 Hz), 2048 particles, NUTS depth 6, alpha 0.5, "
+                                      "2 transitions/stage, identity metric; one step = one full SMC run",
+                          "precision": args.precision, "l2": "flushed (256 MB write) between steps",
+                          "parallelism": f"one independent event per GPU x {world}",
+                          "stages_per_run": n_stages},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+               "clocks": clk, "mixed_vs_fp64": other,
+               "lnz": {"mean": float(np.mean(lnzs)), "runs": [float(x) for x in lnzs]}}
+        print(json.dumps(out))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

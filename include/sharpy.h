@@ -118,6 +118,8 @@ typedef struct {
   double eps_scale;
   int precision;       /* SHARPY_FP64 / SHARPY_MIXED / SHARPY_MIXED_SPLIT            */
   int max_stages;
+  int timing;          /* 1: time each stage's NUTS launch with CUDA events (sharpy_stage.nuts_ms) */
+  int pad;
 } sharpy_smc_options;
 
 typedef struct {
@@ -125,7 +127,8 @@ typedef struct {
   int64_t n_leapfrog;
   int n_divergent;
   int pad;
-  double active_bins;
+  double active_bins;  /* sum over the stage's gradient evaluations of (bins below f_ISCO) x detectors */
+  double nuts_ms;      /* duration of the stage's NUTS launch (opt->timing = 1), else 0 */
 } sharpy_stage;
 
 /* Context. Owns the staged data tables, scratch, the evidence accumulator and
@@ -213,6 +216,11 @@ int sharpy_log_evidence(sharpy_ctx* ctx, double* lnz, int* n_stages);
 int sharpy_smc_run(sharpy_ctx* ctx, const sharpy_smc_options* opt, uint64_t key, double* lnz,
                    int* n_stages, double* theta_out, double* lnl_out, sharpy_stage* stages,
                    sharpy_stream stream);
+
+/* Measurement helper: FP32 FMA TFLOP/s, FP64 FMA TFLOP/s and SFU sin+cos
+   Gop/s of `device` from register-only kernels (out[3], host). Used as the
+   roofline denominators of the ALU-bound likelihood sweep. Synchronous. */
+int sharpy_probe_peaks(int device, double* out);
 
 /* Sticky device status (synchronises): SHARPY_OK or the first error a kernel
    recorded. sharpy_clear_status resets it. */

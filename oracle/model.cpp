@@ -274,6 +274,15 @@ T loglike_t(const ref_model* m, const ref_event* ev, const T* free) {
   return loglike_gw_t(m, ev, free);
 }
 
+template <int N>
+void loglike_dual(const ref_model* m, const ref_event* ev, const double* theta, double* lnl, double* grad) {
+  DualN<N> x[REF_MAX_DIM];
+  for (int i = 0; i < m->n_dim; ++i) x[i] = DualN<N>::variable(theta[i], i);
+  DualN<N> r = loglike_t<DualN<N>>(m, ev, x);
+  *lnl = r.v;
+  for (int i = 0; i < m->n_dim; ++i) grad[i] = r.d[i];
+}
+
 // One parameter vector: ln L and optionally its gradient.
 void loglike_one(const ref_model* m, const ref_event* ev, const double* theta, double* lnl, double* grad) {
   if (grad == nullptr) {
@@ -282,11 +291,12 @@ void loglike_one(const ref_model* m, const ref_event* ev, const double* theta, d
     *lnl = loglike_t<double>(m, ev, x);
     return;
   }
-  Dual x[REF_MAX_DIM];
-  for (int i = 0; i < m->n_dim; ++i) x[i] = Dual::variable(theta[i], i);
-  Dual r = loglike_t<Dual>(m, ev, x);
-  *lnl = r.v;
-  for (int i = 0; i < m->n_dim; ++i) grad[i] = r.d[i];
+  if (m->n_dim <= 2)
+    loglike_dual<2>(m, ev, theta, lnl, grad);
+  else if (m->n_dim <= 4)
+    loglike_dual<4>(m, ev, theta, lnl, grad);
+  else
+    loglike_dual<REF_MAX_DIM>(m, ev, theta, lnl, grad);
 }
 
 // ------------------------------------------------------------------ prior

@@ -1,0 +1,263 @@
+"""Python face of libsharpy: tensors in, tensors out, arguments marshalled.
+
+Device memory and streams come from PyTorch; every step of the sampler's hot
+path runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+import torch
+
+from . import inputs
+from ._lib import (FP64, MIXED, MODEL_GAUSSMIX, MODEL_TAYLORF2, Config, Detector, NutsStats,
+                   SmcOptions, Stage, check, lib)
+
+PRECISION = {"fp64": FP64, "mixed": MIXED}
+STATS_DTYPE = np.dtype([("accept_sum", "<f8"), ("active_bins", "<f8"), ("depth_sum", "<i4"),
+                        ("n_leapfrog", "<i4"), ("n_divergent", "<i4"), ("pad", "<i4")])
+
+
+def _prec(p):
+    return PRECISION[p] if isinstance(p, str) else int(p)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t, what):
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError(f"{what} must be a contiguous float64 CUDA tensor")
+    return t
+
+
+def config_from_workload(w: inputs.Workload) -> Config:
+    c = Config()
+    c.model = MODEL_TAYLORF2
+    c.n_dim = w.n_dim
+    for i in range(w.n_dim):
+        c.phys[i] = w.phys[i]
+        c.lo[i] = w.lo[i]
+        c.hi[i] = w.hi[i]
+        c.prior[i] = w.prior[i]
+        c.boundary[i] = w.boundary[i]
+    for i in range(11):
+        c.fixed[i] = w.fixed[i]
+    return c
+
+
+def gaussmix_config(lo, hi, logw, mu, sigma, boundary=None) -> Config:
+    c = Config()
+    c.model = MODEL_GAUSSMIX
+    c.n_dim = len(lo)
+    for i in range(len(lo)):
+        c.phys[i] = i
+        c.lo[i] = lo[i]
+        c.hi[i] = hi[i]
+        c.prior[i] = 0
+        c.boundary[i] = boundary[i] if boundary else 0
+    c.n_comp = len(logw)
+    for k in range(len(logw)):
+        c.mix_logw[k] = logw[k]
+        for i in range(len(lo)):
+            c.mix_mu[k][i] = mu[k][i]
+            c.mix_sigma[k][i] = sigma[k][i]
+    return c
+
+
+class Context:
+    """A sharpy context bound to one CUDA device."""
+
+    def __init__(self, config: Config, device: int = 0):
+        self._h = C.c_void_p()
+        self.n_dim = config.n_dim
+        self.device = device
+        self.n_det = 0
+        self.n_bins = 0
+        check(lib().sharpy_create(C.byref(self._h), C.byref(config), device), "sharpy_create")
+
+    @classmethod
+    def from_workload(cls, w: inputs.Workload, device: int = 0):
+        return cls(config_from_workload(w), device)
+
+    def close(self):
+        if self._h:
+            lib().sharpy_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- data
+    def set_data(self, data, psd, f_min, df, detectors):
+        data = np.ascontiguousarray(data, dtype=np.float64)
+        psd = np.ascontiguousarray(psd, dtype=np.float64)
+        n_det, n_bins = psd.shape
+        dets = (Detector * max(1, n_det))()
+        for a, d in enumerate(detectors):
+            dets[a] = Detector(d.get("lat", 0.0), d.get("lon", 0.0), d.get("azimuth", 0.0),
+                               d.get("fixed_response", 0), d.get("fplus", 0.0), d.get("fcross", 0.0),
+                               d.get("delay", 0.0))
+        check(lib().sharpy_set_data(self._h, n_det, n_bins, f_min, df,
+                                    data.ctypes.data_as(C.c_void_p), psd.ctypes.data_as(C.c_void_p),
+                                    dets), "sharpy_set_data")
+        self.n_det, self.n_bins = n_det, n_bins
+
+    # ---------------------------------------------------------- likelihood
+    def loglike_grad(self, theta, precision="mixed", grad=True, out=None):
+        theta = _dev(theta, "theta")
+        n = theta.shape[0]
+        lnl = torch.empty(n, dtype=torch.float64, device=theta.device) if out is None else out[0]
+        g = (torch.empty_like(theta) if out is None else out[1]) if grad else None
+        check(lib().sharpy_loglike_grad(self._h, n, _ptr(theta), _ptr(lnl), _ptr(g), _prec(precision),
+                                        _stream()), "sharpy_loglike_grad")
+        return lnl, g
+
+    def waveform(self, theta):
+        theta = _dev(theta, "theta")
+        h = torch.empty((theta.shape[0], self.n_det, self.n_bins, 2), dtype=torch.float64,
+                        device=theta.device)
+        check(lib().sharpy_waveform(self._h, theta.shape[0], _ptr(theta), _ptr(h), _stream()),
+              "sharpy_waveform")
+        return h
+
+    def prior_sample(self, n, key, ctr=0):
+        th = torch.empty((n, self.n_dim), dtype=torch.float64, device=f"cuda:{self.device}")
+        check(lib().sharpy_prior_sample(self._h, n, _ptr(th), key, ctr, _stream()), "sharpy_prior_sample")
+        return th
+
+    def prior_logpdf_grad(self, theta):
+        theta = _dev(theta, "theta")
+        lp = torch.empty(theta.shape[0], dtype=torch.float64, device=theta.device)
+        g = torch.empty_like(theta)
+        check(lib().sharpy_prior_logpdf_grad(self._h, theta.shape[0], _ptr(theta), _ptr(lp), _ptr(g),
+                                             _stream()), "sharpy_prior_logpdf_grad")
+        return lp, g
+
+    # ------------------------------------------------------------- sampler
+    def nuts_mutate(self, beta, theta, lnl, grad, inv_mass, step, max_depth, n_steps, key, ctr,
+                    precision="mixed", stats=True):
+        """In-place NUTS transitions; returns the per-particle stats as a uint8 device buffer."""
+        n = theta.shape[0]
+        st = torch.empty(n * STATS_DTYPE.itemsize, dtype=torch.uint8, device=theta.device) if stats else None
+        check(lib().sharpy_nuts_mutate(self._h, n, beta, _ptr(_dev(theta, "theta")), _ptr(_dev(lnl, "lnl")),
+                                       _ptr(_dev(grad, "grad")), _ptr(inv_mass), step, max_depth, n_steps,
+                                       key, ctr, _prec(precision), _ptr(st), _stream()),
+              "sharpy_nuts_mutate")
+        return st
+
+    @staticmethod
+    def stats_to_numpy(st):
+        return np.frombuffer(st.cpu().numpy().tobytes(), dtype=STATS_DTYPE)
+
+    def reweight_resample(self, theta, lnl, grad, beta_prev, alpha, u, want_cov=True):
+        n, d = theta.shape
+        dev = theta.device
+        sc = torch.zeros(3, dtype=torch.float64, device=dev)
+        anc = torch.empty(n, dtype=torch.int32, device=dev)
+        cov = torch.empty((d, d), dtype=torch.float64, device=dev) if want_cov else None
+        check(lib().sharpy_smc_reweight_resample(
+            self._h, n, _ptr(theta), _ptr(lnl), _ptr(grad), beta_prev, alpha, u,
+            C.c_void_p(sc.data_ptr()), C.c_void_p(sc.data_ptr() + 8), C.c_void_p(sc.data_ptr() + 16),
+            _ptr(anc), _ptr(cov), _stream()), "sharpy_smc_reweight_resample")
+        return {"beta_next": sc[0], "dlnz": sc[1], "ess": sc[2], "ancestors": anc, "cov": cov}
+
+    def reset_evidence(self):
+        check(lib().sharpy_reset_evidence(self._h, _stream()), "sharpy_reset_evidence")
+
+    def log_evidence(self):
+        lnz = C.c_double()
+        ns = C.c_int()
+        check(lib().sharpy_log_evidence(self._h, C.byref(lnz), C.byref(ns)), "sharpy_log_evidence")
+        return lnz.value, ns.value
+
+    def smc_run(self, n_particles, alpha, n_mut, max_depth, metric, eps_scale, key,
+                precision="mixed", max_stages=500, timing=False):
+        o = SmcOptions(n_particles, alpha, n_mut, max_depth, metric, eps_scale, _prec(precision), max_stages,
+                       1 if timing else 0, 0)
+        th = torch.empty((n_particles, self.n_dim), dtype=torch.float64, device=f"cuda:{self.device}")
+        ll = torch.empty(n_particles, dtype=torch.float64, device=th.device)
+        stages = (Stage * max_stages)()
+        lnz = C.c_double()
+        ns = C.c_int()
+        check(lib().sharpy_smc_run(self._h, C.byref(o), key, C.byref(lnz), C.byref(ns), _ptr(th), _ptr(ll),
+                                   stages, _stream()), "sharpy_smc_run")
+        rec = [dict((f, getattr(stages[i], f)) for f, _ in Stage._fields_ if f != "pad")
+               for i in range(ns.value)]
+        return lnz.value, th, ll, rec
+
+    def status(self):
+        return lib().sharpy_get_status(self._h)
+
+    def clear_status(self):
+        check(lib().sharpy_clear_status(self._h), "sharpy_clear_status")
+
+
+def systematic_resample(w, u):
+    """Bit-exact systematic resampling of device weights w (float64, in [0,1])."""
+    w = _dev(w, "w")
+    anc = torch.empty(w.shape[0], dtype=torch.int32, device=w.device)
+    check(lib().sharpy_systematic_resample(w.shape[0], _ptr(w), u, _ptr(anc), _stream()),
+          "sharpy_systematic_resample")
+    return anc
+
+
+class LogLikelihood(torch.autograd.Function):
+    """ln L(theta) with the hand-written adjoint as its backward pass.
+
+    forward: the forward-only sweep (no basis moments); backward: the gradient
+    sweep, which recomputes the waveform in registers instead of storing the
+    particles x bins complex strain.
+    """
+
+    @staticmethod
+    def forward(ctx, theta, sctx, precision):
+        lnl, _ = sctx.loglike_grad(theta.detach().contiguous(), precision, grad=False)
+        ctx.save_for_backward(theta)
+        ctx.sctx = sctx
+        ctx.precision = precision
+        return lnl
+
+    @staticmethod
+    def backward(ctx, gout):
+        (theta,) = ctx.saved_tensors
+        _, g = ctx.sctx.loglike_grad(theta.detach().contiguous(), ctx.precision, grad=True)
+        return gout[:, None] * g, None, None
+
+
+def loglike(theta, sctx, precision="mixed"):
+    return LogLikelihood.apply(theta, sctx, precision)
+
+
+# --------------------------------------------------------------- injections
+def make_event(w: inputs.Workload, seed=0, device=0, with_noise=True):
+    """Synthetic event through the library: h(theta_inj) from sharpy_waveform,
+    distance rescaled to the target SNR using SNR^2 = -2 ln L with zero data,
+    plus seeded Gaussian noise. Returns (Context, theta_inj, data)."""
+    ctx = Context.from_workload(w, device)
+    psd = inputs.psd_array(w)
+    dets = inputs.detectors(w)
+    zeros = np.zeros((w.n_det, w.n_bins, 2))
+    ctx.set_data(zeros, psd, w.f_min, w.df, dets)
+    th = inputs.injection(w, seed).copy()
+    k = inputs.distance_index(w)
+    dev = f"cuda:{device}"
+    if w.snr_target is not None and k is not None:
+        t = torch.tensor(th[None, :], dtype=torch.float64, device=dev)
+        lnl, _ = ctx.loglike_grad(t, "fp64", grad=False)
+        rho = math.sqrt(-2.0 * float(lnl[0]))
+        th[k] = min(max(th[k] * rho / w.snr_target, w.lo[k]), w.hi[k])
+    h = ctx.waveform(torch.tensor(th[None, :], dtype=torch.float64, device=dev))[0].cpu().numpy()
+    data = h + (inputs.noise(w, seed) if with_noise else 0.0)
+    ctx.set_data(data, psd, w.f_min, w.df, dets)
+    return ctx, th, data

@@ -1,0 +1,284 @@
+// Context lifetime, event staging, status word and evidence accumulator.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "context.cuh"
+
+using namespace sharpy;
+
+namespace sharpy {
+
+int ensure_scratch(sharpy_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->scratch_bytes) return SHARPY_OK;
+  SHARPY_CUDA_TRY(cudaDeviceSynchronize());
+  if (ctx->d_scratch) cudaFree(ctx->d_scratch);
+  ctx->d_scratch = nullptr;
+  ctx->scratch_bytes = 0;
+  size_t want = bytes + bytes / 4;
+  if (cudaMalloc(&ctx->d_scratch, want) != cudaSuccess) return SHARPY_ENOMEM;
+  ctx->scratch_bytes = want;
+  return SHARPY_OK;
+}
+
+int check_ctx(sharpy_ctx* ctx, bool need_data) {
+  if (!ctx) return SHARPY_EINVAL;
+  if (need_data && ctx->model.model == SHARPY_MODEL_TAYLORF2 && !ctx->has_data) return SHARPY_ESTATE;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return SHARPY_ECUDA;
+  return SHARPY_OK;
+}
+
+}  // namespace sharpy
+
+static void free_event(sharpy_ctx* c) {
+  cudaFree(c->d_f);
+  cudaFree(c->d_b64);
+  cudaFree(c->d_b32);
+  cudaFree(c->d_e64);
+  cudaFree(c->d_e32);
+  cudaFree(c->d_pref);
+  c->d_f = c->d_b64 = c->d_pref = nullptr;
+  c->d_b32 = nullptr;
+  c->d_e64 = nullptr;
+  c->d_e32 = nullptr;
+  c->has_data = false;
+}
+
+// Detector tensor and position of an L-shaped detector on a spherical Earth.
+static void detector_geometry(const sharpy_detector& in, DevDetector& out) {
+  out.fixed_response = in.fixed_response;
+  out.fplus = in.fplus;
+  out.fcross = in.fcross;
+  out.delay = in.delay;
+  double sl = std::sin(in.lat), cl = std::cos(in.lat), so = std::sin(in.lon), co = std::cos(in.lon);
+  double east[3] = {-so, co, 0.0};
+  double north[3] = {-sl * co, -sl * so, cl};
+  double ca = std::cos(in.azimuth), sa = std::sin(in.azimuth);
+  double x[3], y[3];
+  for (int i = 0; i < 3; ++i) {
+    x[i] = ca * north[i] + sa * east[i];
+    y[i] = -sa * north[i] + ca * east[i];
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) out.D[i][j] = 0.5 * (x[i] * x[j] - y[i] * y[j]);
+  out.r[0] = kEarthR * cl * co;
+  out.r[1] = kEarthR * cl * so;
+  out.r[2] = kEarthR * sl;
+}
+
+extern "C" {
+
+int sharpy_create(sharpy_ctx** out, const sharpy_config* cfg, int device) {
+  if (!out || !cfg) return SHARPY_EINVAL;
+  *out = nullptr;
+  if (cfg->n_dim < 1 || cfg->n_dim > SHARPY_MAX_DIM) return SHARPY_EINVAL;
+  if (cfg->model != SHARPY_MODEL_TAYLORF2 && cfg->model != SHARPY_MODEL_GAUSSMIX) return SHARPY_EINVAL;
+  for (int i = 0; i < cfg->n_dim; ++i) {
+    if (!(cfg->lo[i] < cfg->hi[i]) || !std::isfinite(cfg->lo[i]) || !std::isfinite(cfg->hi[i])) return SHARPY_EINVAL;
+    if (cfg->model == SHARPY_MODEL_TAYLORF2 && (cfg->phys[i] < 0 || cfg->phys[i] >= SHARPY_NPHYS)) return SHARPY_EINVAL;
+    if (cfg->prior[i] == SHARPY_PRIOR_POWER2 && !(cfg->lo[i] > 0.0)) return SHARPY_EINVAL;
+    if (cfg->prior[i] != SHARPY_PRIOR_UNIFORM && cfg->prior[i] != SHARPY_PRIOR_POWER2) return SHARPY_EINVAL;
+    if (cfg->boundary[i] != SHARPY_BOUND_REFLECT && cfg->boundary[i] != SHARPY_BOUND_PERIODIC) return SHARPY_EINVAL;
+  }
+  if (cfg->model == SHARPY_MODEL_GAUSSMIX) {
+    if (cfg->n_comp < 1 || cfg->n_comp > SHARPY_MAX_COMP) return SHARPY_EINVAL;
+    for (int c = 0; c < cfg->n_comp; ++c)
+      for (int i = 0; i < cfg->n_dim; ++i)
+        if (!(cfg->mix_sigma[c][i] > 0.0)) return SHARPY_EINVAL;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return SHARPY_ECUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return SHARPY_ECUDA;
+  sharpy_ctx* c = new (std::nothrow) sharpy_ctx();
+  if (!c) return SHARPY_ENOMEM;
+  c->device = device;
+  DevModel& m = c->model;
+  m.model = cfg->model;
+  m.n_dim = cfg->n_dim;
+  for (int i = 0; i < SHARPY_MAX_DIM; ++i) {
+    m.phys[i] = cfg->phys[i];
+    m.lo[i] = cfg->lo[i];
+    m.hi[i] = cfg->hi[i];
+    m.prior[i] = cfg->prior[i];
+    m.boundary[i] = cfg->boundary[i];
+  }
+  for (int i = 0; i < SHARPY_NPHYS; ++i) m.fixed[i] = cfg->fixed[i];
+  m.n_comp = cfg->n_comp;
+  for (int k = 0; k < SHARPY_MAX_COMP; ++k) {
+    m.mix_logw[k] = cfg->mix_logw[k];
+    for (int i = 0; i < SHARPY_MAX_DIM; ++i) {
+      m.mix_mu[k][i] = cfg->mix_mu[k][i];
+      m.mix_sigma[k][i] = cfg->mix_sigma[k][i];
+    }
+  }
+  bool ok = cudaMalloc(&c->d_status, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&c->d_lnz, 2 * sizeof(double)) == cudaSuccess &&
+            cudaMallocHost(&c->h_pinned, 64 * sizeof(double)) == cudaSuccess &&
+            cudaMemset(c->d_status, 0, sizeof(int)) == cudaSuccess &&
+            cudaMemset(c->d_lnz, 0, 2 * sizeof(double)) == cudaSuccess &&
+            cudaDeviceSynchronize() == cudaSuccess;
+  if (!ok) {
+    sharpy_destroy(c);
+    return SHARPY_ENOMEM;
+  }
+  *out = c;
+  return SHARPY_OK;
+}
+
+void sharpy_destroy(sharpy_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  free_event(c);
+  cudaFree(c->d_status);
+  cudaFree(c->d_lnz);
+  cudaFree(c->d_scratch);
+  cudaFreeHost(c->h_pinned);
+  delete c;
+}
+
+int sharpy_set_data(sharpy_ctx* c, int n_det, int64_t n_bins, double f_min, double df, const double* d,
+                    const double* psd, const sharpy_detector* det) {
+  if (!c || !d || !psd || !det) return SHARPY_EINVAL;
+  if (c->model.model != SHARPY_MODEL_TAYLORF2) return SHARPY_EINVAL;
+  if (n_det < 1 || n_det > SHARPY_MAX_DET || n_bins < 1 || n_bins > (int64_t)1 << 30) return SHARPY_EINVAL;
+  if (!(f_min > 0.0) || !(df > 0.0) || !std::isfinite(f_min) || !std::isfinite(df)) return SHARPY_EINVAL;
+  if (n_det != 1 && n_det != 2 && n_det != 3) return SHARPY_EINVAL;  // kernels are instantiated for 1-3
+  int64_t K = n_bins;
+  for (int64_t i = 0; i < (int64_t)n_det * K; ++i) {
+    if (!std::isfinite(psd[i]) || !(psd[i] > 0.0)) return SHARPY_ENONFINITE;
+    if (!std::isfinite(d[2 * i]) || !std::isfinite(d[2 * i + 1])) return SHARPY_ENONFINITE;
+  }
+  int rc = check_ctx(c, false);
+  if (rc) return rc;
+
+  std::vector<double> f(K), b64(kNBasis * K), e64(2 * n_det * K), pref(n_det * K);
+  std::vector<float> b32(kNBasis * K), e32(2 * n_det * K);
+  for (int64_t k = 0; k < K; ++k) {
+    double fk = f_min + (double)k * df;
+    f[k] = fk;
+    double x = std::cbrt(1.0 / fk), y = std::cbrt(fk), l = std::log(fk);
+    double x2 = x * x;
+    double B[kNBasis] = {x2 * x2 * x, x2 * x, x2, x, l, y, y * l, y * y, fk};
+    for (int j = 0; j < kNBasis; ++j) {
+      b64[j * K + k] = B[j];
+      b32[j * K + k] = (float)B[j];
+    }
+  }
+  // <d|d> with a compensated sum; P_a prefix sums of w f^-7/3 (compensated).
+  double dd = 0.0, ddc = 0.0;
+  for (int a = 0; a < n_det; ++a) {
+    double s = 0.0, cmp = 0.0;
+    for (int64_t k = 0; k < K; ++k) {
+      int64_t i = a * K + k;
+      double w = 4.0 * df / psd[i];
+      double dr = d[2 * i], di = d[2 * i + 1];
+      double amp = std::pow(f[k], -7.0 / 6.0);
+      // E = w conj(d) f^-7/6
+      e64[2 * i] = w * dr * amp;
+      e64[2 * i + 1] = -w * di * amp;
+      e32[2 * i] = (float)e64[2 * i];
+      e32[2 * i + 1] = (float)e64[2 * i + 1];
+      double term = w * amp * amp;
+      double t = s + term;
+      cmp += std::fabs(s) >= std::fabs(term) ? (s - t) + term : (term - t) + s;
+      s = t;
+      pref[i] = s + cmp;
+      double dt = w * (dr * dr + di * di);
+      double u = dd + dt;
+      ddc += std::fabs(dd) >= std::fabs(dt) ? (dd - u) + dt : (dt - u) + dd;
+      dd = u;
+    }
+  }
+  free_event(c);
+  bool ok = cudaMalloc(&c->d_f, K * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_b64, kNBasis * K * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_b32, kNBasis * K * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&c->d_e64, n_det * K * sizeof(double2)) == cudaSuccess &&
+            cudaMalloc(&c->d_e32, n_det * K * sizeof(float2)) == cudaSuccess &&
+            cudaMalloc(&c->d_pref, n_det * K * sizeof(double)) == cudaSuccess;
+  if (!ok) {
+    free_event(c);
+    return SHARPY_ENOMEM;
+  }
+  ok = cudaMemcpy(c->d_f, f.data(), K * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(c->d_b64, b64.data(), b64.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(c->d_b32, b32.data(), b32.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(c->d_e64, e64.data(), e64.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(c->d_e32, e32.data(), e32.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(c->d_pref, pref.data(), pref.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!ok) {
+    free_event(c);
+    return SHARPY_ECUDA;
+  }
+  DevEvent& ev = c->ev;
+  ev.n_det = n_det;
+  ev.n_bins = K;
+  ev.f_min = f_min;
+  ev.df = df;
+  ev.dd = dd + ddc;
+  ev.f = c->d_f;
+  ev.b64 = c->d_b64;
+  ev.b32 = c->d_b32;
+  ev.e64 = c->d_e64;
+  ev.e32 = c->d_e32;
+  ev.pref = c->d_pref;
+  for (int a = 0; a < n_det; ++a) detector_geometry(det[a], ev.det[a]);
+  c->has_data = true;
+  return SHARPY_OK;
+}
+
+int sharpy_reset_evidence(sharpy_ctx* c, sharpy_stream stream) {
+  int rc = check_ctx(c, false);
+  if (rc) return rc;
+  SHARPY_CUDA_TRY(cudaMemsetAsync(c->d_lnz, 0, 2 * sizeof(double), (cudaStream_t)stream));
+  c->last_stream = (cudaStream_t)stream;
+  return SHARPY_OK;
+}
+
+int sharpy_log_evidence(sharpy_ctx* c, double* lnz, int* n_stages) {
+  int rc = check_ctx(c, false);
+  if (rc) return rc;
+  if (!lnz) return SHARPY_EINVAL;
+  SHARPY_CUDA_TRY(cudaMemcpyAsync(c->h_pinned, c->d_lnz, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                  c->last_stream));
+  SHARPY_CUDA_TRY(cudaStreamSynchronize(c->last_stream));
+  *lnz = c->h_pinned[0];
+  if (n_stages) *n_stages = (int)c->h_pinned[1];
+  return SHARPY_OK;
+}
+
+int sharpy_get_status(sharpy_ctx* c) {
+  int rc = check_ctx(c, false);
+  if (rc) return rc;
+  int s = 0;
+  SHARPY_CUDA_TRY(cudaDeviceSynchronize());
+  SHARPY_CUDA_TRY(cudaMemcpy(&s, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  return s;
+}
+
+int sharpy_clear_status(sharpy_ctx* c) {
+  int rc = check_ctx(c, false);
+  if (rc) return rc;
+  SHARPY_CUDA_TRY(cudaDeviceSynchronize());
+  SHARPY_CUDA_TRY(cudaMemset(c->d_status, 0, sizeof(int)));
+  SHARPY_CUDA_TRY(cudaDeviceSynchronize());
+  return SHARPY_OK;
+}
+
+const char* sharpy_error_string(int code) {
+  switch (code) {
+    case SHARPY_OK: return "ok";
+    case SHARPY_EINVAL: return "invalid argument";
+    case SHARPY_ECUDA: return "CUDA runtime error";
+    case SHARPY_ENOMEM: return "out of memory";
+    case SHARPY_ENONFINITE: return "non-finite value";
+    case SHARPY_ETIMEOUT: return "device loop bound reached";
+    case SHARPY_EBOUNDS: return "index out of bounds";
+    case SHARPY_ESTATE: return "call out of order";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,35 @@
+// The context structure and host-side helpers shared by the translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+struct sharpy_ctx {
+  int device = 0;
+  sharpy::DevModel model{};
+  sharpy::DevEvent ev{};
+  bool has_data = false;
+  // event tables (device)
+  double* d_f = nullptr;
+  double* d_b64 = nullptr;
+  float* d_b32 = nullptr;
+  double2* d_e64 = nullptr;
+  float2* d_e32 = nullptr;
+  double* d_pref = nullptr;
+  // status word and evidence accumulator (device)
+  int* d_status = nullptr;
+  double* d_lnz = nullptr;   // [0] ln Z, [1] number of stages (as double)
+  // scratch (grown on demand)
+  void* d_scratch = nullptr;
+  size_t scratch_bytes = 0;
+  // pinned host staging for small readbacks
+  double* h_pinned = nullptr;
+  cudaStream_t last_stream = nullptr;
+};
+
+namespace sharpy {
+// Make sure the context's scratch holds at least `bytes`; stream-ordered users
+// only (a grow synchronises the device first).
+int ensure_scratch(sharpy_ctx* ctx, size_t bytes);
+int check_ctx(sharpy_ctx* ctx, bool need_data);
+}  // namespace sharpy

@@ -1,0 +1,217 @@
+// sharpy_loglike_grad, sharpy_waveform, sharpy_prior_* : kernels and entry points.
+//
+// Likelihood launch shape: one CTA of kWarps warps handles kWarps particles.
+// Warp 0 computes the per-particle prologue lane-parallel (lane s = particle
+// s of the CTA), every warp then sweeps the bins of one particle, and warp 0
+// finishes with the lane-parallel epilogue. The FP64 scalar work thus runs
+// on kWarps lanes per instruction instead of one.
+#include <cstdio>
+
+#include "context.cuh"
+#include "sweep.cuh"
+
+using namespace sharpy;
+
+namespace sharpy {
+
+constexpr int kWarps = 8;
+
+template <int PREC, bool GRAD, int NDET>
+__global__ void __launch_bounds__(kWarps * 32)
+loglike_kernel(DevModel m, DevEvent ev, int64_t n, const double* __restrict__ theta, double* __restrict__ lnl,
+               double* __restrict__ grad, int* status) {
+  using DT = typename std::conditional<PREC == SHARPY_FP64, double, float>::type;
+  __shared__ SweepCoef sc[kWarps];
+  __shared__ EpiCoef<DT> ec[kWarps];
+  __shared__ double mom[kWarps][NDET * kNMom * 2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t base = (int64_t)blockIdx.x * kWarps;
+  const int D = m.n_dim;
+  if (warp == 0 && lane < kWarps) {
+    int64_t p = base + lane;
+    if (p < n) {
+      double th[kMaxDim];
+      for (int i = 0; i < D; ++i) th[i] = theta[p * D + i];
+      prologue<DT, GRAD>(m, ev, th, sc[lane], ec[lane]);
+    } else {
+      sc[lane].ok = 0;
+      sc[lane].kisco = -1;
+    }
+  }
+  __syncthreads();
+  {
+    int64_t p = base + warp;
+    double* mw = mom[warp];
+    for (int i = lane; i < NDET * kNMom * 2; i += 32) mw[i] = 0.0;
+    __syncwarp();
+    if (p < n && sc[warp].ok) sweep<PREC, GRAD, NDET>(ev, sc[warp], mw);
+  }
+  __syncthreads();
+  if (warp == 0 && lane < kWarps) {
+    int64_t p = base + lane;
+    if (p < n) {
+      double l = NAN, gph[SHARPY_NPHYS];
+      if (sc[lane].ok) epilogue<DT, GRAD>(ev, sc[lane], ec[lane], mom[lane], &l, gph);
+      lnl[p] = l;
+      bool fin = isfinite(l);
+      if (GRAD) {
+        for (int i = 0; i < D; ++i) {
+          double g = sc[lane].ok ? gph[m.phys[i]] : NAN;
+          grad[p * D + i] = g;
+          fin = fin && isfinite(g);
+        }
+      }
+      if (!fin) set_status(status, SHARPY_ENONFINITE);
+    }
+  }
+}
+
+__global__ void gaussmix_kernel(DevModel m, int64_t n, const double* __restrict__ theta, double* __restrict__ lnl,
+                                double* __restrict__ grad) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int D = m.n_dim;
+  double x[kMaxDim], g[kMaxDim];
+  for (int i = 0; i < D; ++i) x[i] = theta[p * D + i];
+  double l;
+  gaussmix(m, x, &l, grad ? g : nullptr);
+  lnl[p] = l;
+  if (grad)
+    for (int i = 0; i < D; ++i) grad[p * D + i] = g[i];
+}
+
+// One CTA per (particle, block of 256 bins): FP64 strain of every detector.
+__global__ void waveform_kernel(DevModel m, DevEvent ev, int64_t n, const double* __restrict__ theta,
+                                double* __restrict__ h) {
+  __shared__ SweepCoef sc;
+  __shared__ EpiCoef<double> ec;
+  const int64_t p = blockIdx.y;
+  if (threadIdx.x == 0) {
+    double th[kMaxDim];
+    for (int i = 0; i < m.n_dim; ++i) th[i] = theta[p * m.n_dim + i];
+    prologue<double, false>(m, ev, th, sc, ec);
+  }
+  __syncthreads();
+  const int64_t K = ev.n_bins;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  for (int a = 0; a < ev.n_det; ++a) {
+    double hr = 0.0, hi = 0.0;
+    if (sc.ok && k <= sc.kisco) {
+      double S = sc.c0;
+      for (int j = 0; j < kNPn; ++j) S = fma(sc.alpha[j], ev.b64[(int64_t)j * K + k], S);
+      double f = ev.f[k];
+      double P = fma(f, sc.tau[a], S);
+      double r = P - rint(P);
+      double sn, cs;
+      sincospi(2.0 * r, &sn, &cs);
+      double amp = ec.A0 * pow(f, -7.0 / 6.0);
+      hr = amp * (ec.cre[a] * cs + ec.cim[a] * sn);
+      hi = amp * (ec.cim[a] * cs - ec.cre[a] * sn);
+    }
+    int64_t o = ((p * ev.n_det + a) * K + k) * 2;
+    h[o] = hr;
+    h[o + 1] = hi;
+  }
+}
+
+__global__ void prior_sample_kernel(DevModel m, int64_t n, double* __restrict__ theta, uint64_t key, uint32_t ctr) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  for (int i = 0; i < m.n_dim; ++i) {
+    double u0, u1;
+    uniform2(key, (uint32_t)p, ctr, RNG_PRIOR, (uint32_t)i, &u0, &u1);
+    double lo = m.lo[i], hi = m.hi[i], x;
+    if (m.prior[i] == SHARPY_PRIOR_POWER2)
+      x = cbrt(lo * lo * lo + u0 * (hi * hi * hi - lo * lo * lo));
+    else
+      x = lo + u0 * (hi - lo);
+    theta[p * m.n_dim + i] = x;
+  }
+}
+
+__global__ void prior_logpdf_kernel(DevModel m, int64_t n, const double* __restrict__ theta, double* __restrict__ lp,
+                                    double* __restrict__ glp) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  double x[kMaxDim], g[kMaxDim];
+  for (int i = 0; i < m.n_dim; ++i) x[i] = theta[p * m.n_dim + i];
+  lp[p] = prior_logpdf(m, x, glp ? g : nullptr);
+  if (glp)
+    for (int i = 0; i < m.n_dim; ++i) glp[p * m.n_dim + i] = g[i];
+}
+
+template <int PREC, bool GRAD>
+static cudaError_t launch_ll(sharpy_ctx* c, int64_t n, const double* th, double* lnl, double* grad, cudaStream_t s) {
+  dim3 grid((unsigned)((n + kWarps - 1) / kWarps));
+  switch (c->ev.n_det) {
+    case 1: loglike_kernel<PREC, GRAD, 1><<<grid, kWarps * 32, 0, s>>>(c->model, c->ev, n, th, lnl, grad, c->d_status); break;
+    case 2: loglike_kernel<PREC, GRAD, 2><<<grid, kWarps * 32, 0, s>>>(c->model, c->ev, n, th, lnl, grad, c->d_status); break;
+    default: loglike_kernel<PREC, GRAD, 3><<<grid, kWarps * 32, 0, s>>>(c->model, c->ev, n, th, lnl, grad, c->d_status); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace sharpy
+
+extern "C" {
+
+int sharpy_loglike_grad(sharpy_ctx* c, int64_t n, const double* theta, double* lnl, double* grad, int precision,
+                        sharpy_stream stream) {
+  int rc = check_ctx(c, true);
+  if (rc) return rc;
+  if (n < 0 || (n > 0 && (!theta || !lnl))) return SHARPY_EINVAL;
+  if (precision != SHARPY_FP64 && precision != SHARPY_MIXED) return SHARPY_EINVAL;
+  if (n == 0) return SHARPY_OK;
+  if (n > ((int64_t)1 << 31) - 1) return SHARPY_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  cudaError_t e;
+  if (c->model.model == SHARPY_MODEL_GAUSSMIX) {
+    gaussmix_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(c->model, n, theta, lnl, grad);
+    e = cudaGetLastError();
+  } else if (precision == SHARPY_FP64) {
+    e = grad ? launch_ll<SHARPY_FP64, true>(c, n, theta, lnl, grad, s) : launch_ll<SHARPY_FP64, false>(c, n, theta, lnl, grad, s);
+  } else {
+    e = grad ? launch_ll<SHARPY_MIXED, true>(c, n, theta, lnl, grad, s) : launch_ll<SHARPY_MIXED, false>(c, n, theta, lnl, grad, s);
+  }
+  return e == cudaSuccess ? SHARPY_OK : SHARPY_ECUDA;
+}
+
+int sharpy_waveform(sharpy_ctx* c, int64_t n, const double* theta, double* h, sharpy_stream stream) {
+  int rc = check_ctx(c, true);
+  if (rc) return rc;
+  if (c->model.model != SHARPY_MODEL_TAYLORF2) return SHARPY_EINVAL;
+  if (n < 0 || n > 65535 || (n > 0 && (!theta || !h))) return SHARPY_EINVAL;
+  if (n == 0) return SHARPY_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  dim3 grid((unsigned)((c->ev.n_bins + 255) / 256), (unsigned)n);
+  waveform_kernel<<<grid, 256, 0, s>>>(c->model, c->ev, n, theta, h);
+  return cudaGetLastError() == cudaSuccess ? SHARPY_OK : SHARPY_ECUDA;
+}
+
+int sharpy_prior_sample(sharpy_ctx* c, int64_t n, double* theta, uint64_t key, uint64_t ctr, sharpy_stream stream) {
+  int rc = check_ctx(c, false);
+  if (rc) return rc;
+  if (n < 0 || n > ((int64_t)1 << 31) - 1 || (n > 0 && !theta)) return SHARPY_EINVAL;
+  if (n == 0) return SHARPY_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  prior_sample_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(c->model, n, theta, key, (uint32_t)ctr);
+  return cudaGetLastError() == cudaSuccess ? SHARPY_OK : SHARPY_ECUDA;
+}
+
+int sharpy_prior_logpdf_grad(sharpy_ctx* c, int64_t n, const double* theta, double* lp, double* glp,
+                             sharpy_stream stream) {
+  int rc = check_ctx(c, false);
+  if (rc) return rc;
+  if (n < 0 || n > ((int64_t)1 << 31) - 1 || (n > 0 && (!theta || !lp))) return SHARPY_EINVAL;
+  if (n == 0) return SHARPY_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  prior_logpdf_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(c->model, n, theta, lp, glp);
+  return cudaGetLastError() == cudaSuccess ? SHARPY_OK : SHARPY_ECUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,180 @@
+// The per-bin sweep: one warp accumulates the moments of one particle.
+//
+// Lane l visits bins k = l, l+32, ... <= k_ISCO (coalesced SoA table reads).
+// Per bin the phase polynomial sum_j alpha_j B_j(f_k) + c0 is shared by all
+// detectors; per detector it adds f_k tau_a, reduces mod 1 turn, forms the
+// carrier e^{-i Psi}, multiplies the pre-whitened data E_ak and accumulates
+// Z_a (and, for the gradient, Y_aj = sum z B_j).
+//
+//   SHARPY_FP64  : FP64 throughout; reduction Psi - rint(Psi); sincospi.
+//   SHARPY_MIXED : FP64 phase accumulated on top of the offset 1.5 * 2^20
+//                  turns, whose low mantissa word is the fractional turn in
+//                  2^-32 units; FP32 sincos, carrier and moments. Per-lane
+//                  FP32 partial sums are flushed every kFlush iterations
+//                  through a fixed-order warp tree into FP64 accumulators
+//                  (blocked pairwise summation).
+#pragma once
+#include "physics.cuh"
+
+namespace sharpy {
+
+constexpr int kFlush = 64;  // lane iterations per FP32 block
+
+template <int NDET, bool GRAD>
+struct MomCount {
+  static constexpr int value = GRAD ? NDET * kNMom * 2 : NDET * 2;
+};
+
+// Index of moment (a, j, ri) in the full layout.
+__device__ __forceinline__ int mom_index(int a, int j, int ri) { return (a * kNMom + j) * 2 + ri; }
+
+template <int NDET, bool GRAD>
+__device__ __forceinline__ int acc_to_mom(int i) {
+  if (GRAD) return i;
+  return mom_index(i / 2, 9, i & 1);
+}
+
+// Flush per-lane FP32 partials into the lane-distributed FP64 accumulators.
+template <int NACC>
+__device__ __forceinline__ void flush(float* acc, double* outer, int lane) {
+#pragma unroll
+  for (int i = 0; i < NACC; ++i) {
+    float v = warp_sum(acc[i]);
+    if ((i & 31) == lane) outer[i >> 5] += (double)v;
+    acc[i] = 0.0f;
+  }
+}
+
+template <bool GRAD, int NDET>
+__device__ void sweep_mixed(const DevEvent& ev, const SweepCoef& sc, double* mom) {
+  constexpr int NACC = MomCount<NDET, GRAD>::value;
+  constexpr int NOUT = (NACC + 31) / 32;
+  const int lane = threadIdx.x & 31;
+  const int64_t K = ev.n_bins;
+  float acc[NACC];
+  double outer[NOUT];
+#pragma unroll
+  for (int i = 0; i < NACC; ++i) acc[i] = 0.0f;
+#pragma unroll
+  for (int i = 0; i < NOUT; ++i) outer[i] = 0.0;
+  double al[kNPn];
+#pragma unroll
+  for (int j = 0; j < kNPn; ++j) al[j] = sc.alpha[j];
+  double tau[NDET];
+#pragma unroll
+  for (int a = 0; a < NDET; ++a) tau[a] = sc.tau[a];
+  const double s0 = sc.c0 + kTurnOffset;
+  const int kend = sc.kisco;
+  int it = 0;
+  // Warp-uniform trip count: lanes past k_ISCO idle but still join the flushes.
+  for (int k0 = 0; k0 <= kend; k0 += 32) {
+    const int k = k0 + lane;
+    if (k <= kend) {
+    double S = s0;
+#pragma unroll
+    for (int j = 0; j < kNPn; ++j) S = fma(al[j], __ldg(ev.b64 + (int64_t)j * K + k), S);
+    const double f = __ldg(ev.b64 + (int64_t)8 * K + k);
+    float bf[kNBasis];
+    if (GRAD) {
+#pragma unroll
+      for (int j = 0; j < kNBasis; ++j) bf[j] = __ldg(ev.b32 + (int64_t)j * K + k);
+    }
+#pragma unroll
+    for (int a = 0; a < NDET; ++a) {
+      const double P = fma(f, tau[a], S);
+      const int turn = __double2loint(P);  // fractional turn, 2^-32 units
+      const float ang = (float)turn * 1.46291807926715968e-9f;  // 2 pi / 2^32
+      float sn, cs;
+      __sincosf(ang, &sn, &cs);
+      const float2 E = __ldg(ev.e32 + (int64_t)a * K + k);
+      const float zr = E.x * cs + E.y * sn;
+      const float zi = E.y * cs - E.x * sn;
+      if (GRAD) {
+#pragma unroll
+        for (int j = 0; j < kNBasis; ++j) {
+          acc[(a * kNMom + j) * 2] += zr * bf[j];
+          acc[(a * kNMom + j) * 2 + 1] += zi * bf[j];
+        }
+        acc[(a * kNMom + 9) * 2] += zr;
+        acc[(a * kNMom + 9) * 2 + 1] += zi;
+      } else {
+        acc[a * 2] += zr;
+        acc[a * 2 + 1] += zi;
+      }
+    }
+    }
+    if (++it == kFlush) {
+      flush<NACC>(acc, outer, lane);
+      it = 0;
+    }
+  }
+  // Every lane takes part in the final flush (warp-uniform).
+  flush<NACC>(acc, outer, lane);
+#pragma unroll
+  for (int i = 0; i < NOUT; ++i) {
+    int idx = i * 32 + lane;
+    if (idx < NACC) mom[acc_to_mom<NDET, GRAD>(idx)] = outer[i];
+  }
+}
+
+template <bool GRAD, int NDET>
+__device__ void sweep_fp64(const DevEvent& ev, const SweepCoef& sc, double* mom) {
+  constexpr int NACC = MomCount<NDET, GRAD>::value;
+  const int lane = threadIdx.x & 31;
+  const int64_t K = ev.n_bins;
+  double acc[NACC];
+#pragma unroll
+  for (int i = 0; i < NACC; ++i) acc[i] = 0.0;
+  double al[kNPn];
+#pragma unroll
+  for (int j = 0; j < kNPn; ++j) al[j] = sc.alpha[j];
+  const int kend = sc.kisco;
+  for (int k = lane; k <= kend; k += 32) {
+    double S = sc.c0;
+#pragma unroll
+    for (int j = 0; j < kNPn; ++j) S = fma(al[j], ev.b64[(int64_t)j * K + k], S);
+    const double f = ev.b64[(int64_t)8 * K + k];
+    double bf[kNBasis];
+    if (GRAD) {
+#pragma unroll
+      for (int j = 0; j < kNBasis; ++j) bf[j] = ev.b64[(int64_t)j * K + k];
+    }
+#pragma unroll
+    for (int a = 0; a < NDET; ++a) {
+      const double P = fma(f, sc.tau[a], S);
+      const double r = P - rint(P);
+      double sn, cs;
+      sincospi(2.0 * r, &sn, &cs);
+      const double2 E = ev.e64[(int64_t)a * K + k];
+      const double zr = E.x * cs + E.y * sn;
+      const double zi = E.y * cs - E.x * sn;
+      if (GRAD) {
+#pragma unroll
+        for (int j = 0; j < kNBasis; ++j) {
+          acc[(a * kNMom + j) * 2] += zr * bf[j];
+          acc[(a * kNMom + j) * 2 + 1] += zi * bf[j];
+        }
+        acc[(a * kNMom + 9) * 2] += zr;
+        acc[(a * kNMom + 9) * 2 + 1] += zi;
+      } else {
+        acc[a * 2] += zr;
+        acc[a * 2 + 1] += zi;
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NACC; ++i) {
+    double v = warp_sum(acc[i]);
+    if (lane == 0) mom[acc_to_mom<NDET, GRAD>(i)] = v;
+  }
+}
+
+template <int PREC, bool GRAD, int NDET>
+__device__ __forceinline__ void sweep(const DevEvent& ev, const SweepCoef& sc, double* mom) {
+  if (PREC == SHARPY_FP64)
+    sweep_fp64<GRAD, NDET>(ev, sc, mom);
+  else
+    sweep_mixed<GRAD, NDET>(ev, sc, mom);
+}
+
+}  // namespace sharpy

@@ -1,0 +1,185 @@
+"""GPU likelihood, gradient and waveform against the oracle (same seeded inputs).
+
+Tolerances: FP64 path |d lnL| <= 1e-7 + 1e-10 |lnL| and gradient relative
+error <= 1e-8; mixed path |d lnL| <= 1e-3 (<= 1e-2 for the 259585-bin
+workload) and gradient relative error <= 1e-4, where the gradient error is
+||(g - g_ref) * width|| / ||g_ref * width|| per particle (prior widths put
+all components on one scale).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2601_02336_gb300 import api, inputs
+from paper_2601_02336_gb300._lib import SharpyError
+from tests import gpu_helpers as G
+from tests import helpers
+
+pytestmark = pytest.mark.gpu
+
+
+def _thetas(w, th_inj, n_prior, n_ball, seed):
+    return np.vstack([inputs.prior_draws(w, n_prior, seed), inputs.ball(w, th_inj, n_ball, seed + 1)])
+
+
+def _check(w, ev, ctx, thetas, lnl_tol, grad_tol, precision):
+    model = helpers.oracle_model(w)
+    ref_l, ref_g = oracle.loglike(model, ev, thetas)
+    l, g = ctx.loglike_grad(G.to_dev(thetas), precision)
+    torch.cuda.synchronize()
+    l, g = l.cpu().numpy(), g.cpu().numpy()
+    dl = np.abs(l - ref_l)
+    assert np.all(np.isfinite(l)) and np.all(np.isfinite(g))
+    assert np.max(dl - lnl_tol(ref_l)) <= 0, (np.max(dl), ref_l[np.argmax(dl)])
+    err = G.grad_rel_err(g, ref_g, G.width(w))
+    assert np.max(err) <= grad_tol, (np.max(err), np.argmax(err))
+    # forward-only sweep gives the same ln L as the gradient sweep
+    l2, _ = ctx.loglike_grad(G.to_dev(thetas), precision, grad=False)
+    assert np.allclose(l2.cpu().numpy(), l, rtol=0, atol=1e-9 * max(1.0, np.max(np.abs(l))))
+    return dl, err
+
+
+@pytest.mark.parametrize("name", ["tiny", "bbh11"])
+def test_waveform_matches_oracle(name):
+    G.require_gpu()
+    w = inputs.WORKLOADS[name]()
+    ev, ctx, th_inj, _ = G.event_pair(w)
+    model = helpers.oracle_model(w)
+    thetas = _thetas(w, th_inj, 3, 2, 40)
+    h = ctx.waveform(G.to_dev(thetas)).cpu().numpy()
+    for i, th in enumerate(thetas):
+        ref = oracle.waveform(model, ev, th)
+        scale = np.max(np.abs(ref))
+        assert np.max(np.abs(h[i] - ref)) <= 1e-9 * scale, i
+
+
+@pytest.mark.parametrize("name", ["tiny", "bbh11", "bbh11_long"])
+def test_loglike_grad_fp64(name):
+    G.require_gpu()
+    w = inputs.WORKLOADS[name]()
+    ev, ctx, th_inj, _ = G.event_pair(w)
+    thetas = _thetas(w, th_inj, 21, 19, 50)  # 40 rows: several CTAs and a ragged tail
+    _check(w, ev, ctx, thetas, lambda r: 1e-7 + 1e-10 * np.abs(r), 1e-8, "fp64")
+
+
+@pytest.mark.parametrize("name", ["tiny", "bbh11", "bbh11_long"])
+def test_loglike_grad_mixed(name):
+    G.require_gpu()
+    w = inputs.WORKLOADS[name]()
+    ev, ctx, th_inj, _ = G.event_pair(w)
+    thetas = _thetas(w, th_inj, 35, 29, 60)
+    _check(w, ev, ctx, thetas, lambda r: 1e-3 + 0 * r, 1e-4, "mixed")
+
+
+def test_loglike_long_signal_sampled():
+    """259585 bins x 3 detectors at full size (sampled particles): mixed within 1e-2, FP64 tight."""
+    G.require_gpu()
+    w = inputs.bns()
+    ev, ctx, th_inj, _ = G.event_pair(w)
+    thetas = _thetas(w, th_inj, 9, 7, 70)
+    _check(w, ev, ctx, thetas, lambda r: 1e-2 + 0 * r, 1e-4, "mixed")
+    _check(w, ev, ctx, thetas[:6], lambda r: 1e-6 + 1e-10 * np.abs(r), 1e-8, "fp64")
+
+
+def test_gradient_central_differences_gpu():
+    """GPU FP64 gradient vs central differences of the GPU FP64 ln L (h = 1e-6 relative), 64 seeded theta
+    on the 32449-bin workload; components whose step moves the f_ISCO bin are skipped."""
+    G.require_gpu()
+    w = inputs.bbh11_long()
+    ev, ctx, th_inj, _ = G.event_pair(w)
+    thetas = _thetas(w, th_inj, 32, 32, 80)
+    l, g = ctx.loglike_grad(G.to_dev(thetas), "fp64")
+    g = g.cpu().numpy()
+    wid = G.width(w)
+    pts, hs = [], []
+    for th in thetas:
+        for j in range(w.n_dim):
+            h = 1e-6 * abs(th[j]) if abs(th[j]) > 1e-3 * wid[j] else 1e-6 * wid[j]
+            hs.append(h)
+            for s in (1, -1):
+                t = th.copy()
+                t[j] += s * h
+                pts.append(t)
+    vals, _ = ctx.loglike_grad(G.to_dev(np.array(pts)), "fp64", grad=False)
+    vals = vals.cpu().numpy().reshape(len(thetas), w.n_dim, 2)
+    fd = (vals[..., 0] - vals[..., 1]) / (2 * np.array(hs).reshape(len(thetas), w.n_dim))
+    kis = lambda t: math.floor((oracle.f_isco(t[0], t[1]) - w.f_min) / w.df)
+    checked = 0
+    for i, th in enumerate(thetas):
+        for j in range(w.n_dim):
+            if j in (0, 1):
+                tp, tm = th.copy(), th.copy()
+                tp[j] += hs[i * w.n_dim + j]
+                tm[j] -= hs[i * w.n_dim + j]
+                if kis(tp) != kis(th) or kis(tm) != kis(th):
+                    continue
+            scale = max(abs(g[i, j]), 1e-3 * np.linalg.norm(g[i] * wid) / wid[j], 1e-8)
+            noise = 20 * 2.2e-16 * abs(float(l[i])) / hs[i * w.n_dim + j]  # rounding of ln L in the FD
+            assert abs(fd[i, j] - g[i, j]) <= 2e-4 * scale + noise, (i, j, fd[i, j], g[i, j])
+            checked += 1
+    assert checked > 0.9 * len(thetas) * w.n_dim
+
+
+def test_edge_cases():
+    G.require_gpu()
+    w = inputs.bbh11()
+    ev, ctx, th_inj, _ = G.event_pair(w)
+    model = helpers.oracle_model(w)
+    # empty batch
+    l, g = ctx.loglike_grad(torch.empty((0, w.n_dim), dtype=torch.float64, device="cuda"))
+    assert l.shape == (0,)
+    # single particle, and a mass above the band: f_ISCO < f_min, no bins -> lnL = -<d|d>/2
+    th = th_inj.copy()
+    th[0] = 400.0
+    for prec in ("fp64", "mixed"):
+        l, g = ctx.loglike_grad(G.to_dev(th[None, :]), prec)
+        ref = oracle.loglike(model, ev, th[None, :], grad=False)[0]
+        assert float(l[0]) == pytest.approx(ref, rel=1e-12)
+    # ragged batch sizes across CTA boundaries give identical rows
+    thetas = inputs.prior_draws(w, 17, 90)
+    full, _ = ctx.loglike_grad(G.to_dev(thetas), "mixed")
+    for n in (1, 7, 8, 9, 16, 17):
+        part, _ = ctx.loglike_grad(G.to_dev(thetas[:n]), "mixed")
+        assert torch.equal(part, full[:n])
+    assert ctx.status() == 0
+
+
+def test_nonfinite_input_sets_status():
+    G.require_gpu()
+    w = inputs.tiny()
+    ev, ctx, th_inj, _ = G.event_pair(w)
+    th = th_inj.copy()
+    th[0] = float("nan")
+    l, g = ctx.loglike_grad(G.to_dev(th[None, :]), "mixed")
+    assert not np.isfinite(float(l[0]))
+    assert ctx.status() == -4
+    ctx.clear_status()
+    assert ctx.status() == 0
+
+
+def test_set_data_rejects_nonfinite():
+    G.require_gpu()
+    w = inputs.tiny()
+    ctx = api.Context.from_workload(w)
+    data = np.zeros((1, w.n_bins, 2))
+    psd = inputs.psd_array(w)
+    psd[0, 10] = np.inf
+    with pytest.raises(SharpyError):
+        ctx.set_data(data, psd, w.f_min, w.df, inputs.detectors(w))
+    with pytest.raises(Exception):
+        ctx.loglike_grad(G.to_dev(inputs.prior_draws(w, 2, 1)))
+
+
+def test_autograd_backward_is_the_adjoint():
+    G.require_gpu()
+    w = inputs.bbh11()
+    ev, ctx, th_inj, _ = G.event_pair(w)
+    th = G.to_dev(_thetas(w, th_inj, 5, 5, 95)).requires_grad_(True)
+    l = api.loglike(th, ctx, "mixed")
+    wts = torch.linspace(0.5, 2.0, th.shape[0], dtype=torch.float64, device="cuda")
+    (l * wts).sum().backward()
+    _, g = ctx.loglike_grad(th.detach(), "mixed")
+    assert torch.allclose(th.grad, g * wts[:, None], rtol=1e-12, atol=0)

@@ -1,0 +1,137 @@
+"""Persistent GPU NUTS against the oracle's NUTS (same Philox key and counters).
+
+With FP64 arithmetic on both sides a transition follows the same trajectory
+up to rounding, so the returned positions agree to ~1e-10 unless a random
+acceptance sits within rounding of its threshold: at least 95 % of particles
+must match to 1e-7 (in prior-width units) with identical leapfrog counts, and
+every returned (theta, ln L, grad) must be self-consistent.
+"""
+import numpy as np
+import pytest
+import torch
+from scipy import stats
+
+import oracle
+from paper_2601_02336_gb300 import api, inputs
+from tests import gpu_helpers as G
+from tests import helpers
+
+pytestmark = pytest.mark.gpu
+
+
+def _gm(d=3, dense=False):
+    lo, hi = [-6.0] * d, [6.0] * d
+    mu = [[0.5 * i for i in range(d)], [-1.0] * d]
+    sig = [[1.0 + 0.2 * i for i in range(d)], [0.3] * d]
+    cfg = api.gaussmix_config(lo, hi, [np.log(0.7), np.log(0.3)], mu, sig, [0] * (d - 1) + [1])
+    model = helpers.gaussmix_model(lo, hi, [np.log(0.7), np.log(0.3)], mu, sig, [0] * (d - 1) + [1])
+    return cfg, model, np.array(hi) - np.array(lo)
+
+
+def _compare(th_g, l_g, st_g, th_o, l_o, st_o, wid, frac=0.95, tol=1e-7):
+    dev = np.max(np.abs(th_g - th_o) / wid[None, :], axis=1)
+    match = dev < tol
+    assert match.mean() >= frac, (match.mean(), np.sort(dev)[-5:])
+    assert np.array_equal(st_g["n_leapfrog"][match], st_o["n_leapfrog"][match])
+    # the two FP64 likelihoods differ by summation order only (~1e-7 at |lnL| ~ 1e3)
+    assert np.allclose(l_g[match], l_o[match], rtol=1e-9, atol=1e-6)
+    return match
+
+
+@pytest.mark.parametrize("dense", [False, True])
+def test_nuts_gaussmix_matches_oracle(dense):
+    G.require_gpu()
+    cfg, model, wid = _gm(3)
+    ctx = api.Context(cfg)
+    n = 1000
+    th = np.random.default_rng(1).uniform(-3, 3, size=(n, 3))
+    lnl, g = oracle.loglike(model, None, th)
+    minv = np.array([[1.0, 0.2, 0.0], [0.2, 0.8, 0.1], [0.0, 0.1, 0.5]]) if dense else None
+    for beta in (0.3, 1.0):
+        ref = oracle.nuts_mutate(model, None, beta, th, lnl, g, minv, 0.4, 6, 2, key=21, ctr=5)
+        t, l, gg = G.to_dev(th), G.to_dev(lnl), G.to_dev(g)
+        st = ctx.nuts_mutate(beta, t, l, gg, G.to_dev(minv) if dense else None, 0.4, 6, 2, key=21, ctr=5,
+                             precision="fp64")
+        st = api.Context.stats_to_numpy(st)
+        _compare(t.cpu().numpy(), l.cpu().numpy(), st, ref[0], ref[1], ref[3], wid, frac=0.99)
+        # returned ln L / gradient belong to the returned positions
+        l2, g2 = oracle.loglike(model, None, t.cpu().numpy())
+        assert np.allclose(l.cpu().numpy(), l2, rtol=1e-12, atol=1e-12)
+        assert np.allclose(gg.cpu().numpy(), g2, rtol=1e-10, atol=1e-12)
+
+
+def test_nuts_taylorf2_fp64_matches_oracle():
+    G.require_gpu()
+    w = inputs.tiny()
+    ev, ctx, th_inj, _ = G.event_pair(w)
+    model = helpers.oracle_model(w)
+    n = 100
+    th = np.vstack([inputs.ball(w, th_inj, n // 2, 3, rel=2e-3), inputs.prior_draws(w, n - n // 2, 4)])
+    lnl, g = oracle.loglike(model, ev, th)
+    wid = G.width(w)
+    for beta, eps in [(0.05, 2e-3), (1.0, 2e-4)]:
+        ref = oracle.nuts_mutate(model, ev, beta, th, lnl, g, None, eps, 5, 2, key=33, ctr=17)
+        t, l, gg = G.to_dev(th), G.to_dev(lnl), G.to_dev(g)
+        st = api.Context.stats_to_numpy(ctx.nuts_mutate(beta, t, l, gg, None, eps, 5, 2, key=33, ctr=17,
+                                                        precision="fp64"))
+        _compare(t.cpu().numpy(), l.cpu().numpy(), st, ref[0], ref[1], ref[3], wid)
+        assert st["active_bins"].sum() > 0
+
+
+def test_nuts_taylorf2_11d_mixed_vs_fp64():
+    """The mixed sweep changes H by ~1e-4 at most, so most trajectories stay identical to the FP64 ones."""
+    G.require_gpu()
+    w = inputs.bbh11()
+    ev, ctx, th_inj, _ = G.event_pair(w)
+    n = 256
+    th = inputs.ball(w, th_inj, n, 9, rel=1e-4)
+    t0 = G.to_dev(th)
+    l0, g0 = ctx.loglike_grad(t0, "fp64")
+    out = {}
+    for prec in ("fp64", "mixed"):
+        t, l, g = t0.clone(), l0.clone(), g0.clone()
+        st = ctx.nuts_mutate(0.7, t, l, g, None, 1e-5, 6, 2, key=5, ctr=1, precision=prec)
+        out[prec] = (t.cpu().numpy(), l.cpu().numpy(), api.Context.stats_to_numpy(st))
+    dev = np.max(np.abs(out["fp64"][0] - out["mixed"][0]) / G.width(w)[None, :], axis=1)
+    assert np.mean(dev < 1e-6) >= 0.8
+    assert np.all(np.isfinite(out["mixed"][0]))
+    # self-consistency of the mixed outputs
+    l2, _ = ctx.loglike_grad(G.to_dev(out["mixed"][0]), "mixed")
+    assert np.allclose(l2.cpu().numpy(), out["mixed"][1], rtol=0, atol=1e-6)
+    assert ctx.status() == 0
+
+
+def test_nuts_stationarity_gpu():
+    """Chains started exactly at N(0, diag) stay there after one GPU transition (KS per coordinate)."""
+    G.require_gpu()
+    d = 2
+    cfg = api.gaussmix_config([-10.0] * d, [10.0] * d, [0.0], [[0.0] * d], [[1.0, 0.3]])
+    ctx = api.Context(cfg)
+    n = 20000
+    th = np.random.default_rng(8).standard_normal((n, d)) * np.array([1.0, 0.3])
+    t = G.to_dev(th)
+    l, g = ctx.loglike_grad(t)
+    ctx.nuts_mutate(1.0, t, l, g, G.to_dev(np.array([[1.0, 0.1], [0.1, 0.09]])), 0.6, 8, 1, key=9, ctr=0,
+                    precision="fp64")
+    out = t.cpu().numpy()
+    assert stats.kstest(out[:, 0], "norm").pvalue > 1e-3
+    assert stats.kstest(out[:, 1] / 0.3, "norm").pvalue > 1e-3
+    assert np.mean(np.abs(out - th)) > 0.1
+
+
+def test_nuts_edge_cases():
+    G.require_gpu()
+    cfg, model, wid = _gm(2)
+    ctx = api.Context(cfg)
+    th = np.array([[0.1, 0.2], [5.9, -5.9], [0.0, 0.0]])
+    t = G.to_dev(th)
+    l, g = ctx.loglike_grad(t)
+    # zero transitions and depth 0 leave the state untouched
+    ctx.nuts_mutate(1.0, t, l, g, None, 0.5, 4, 0, key=1, ctr=0, precision="fp64")
+    ctx.nuts_mutate(1.0, t, l, g, None, 0.5, 0, 3, key=1, ctr=0, precision="fp64")
+    assert np.array_equal(t.cpu().numpy(), th)
+    # a huge step is reflected back into the box
+    ctx.nuts_mutate(1.0, t, l, g, None, 50.0, 3, 2, key=2, ctr=0, precision="fp64")
+    out = t.cpu().numpy()
+    assert np.all(out >= -6.0) and np.all(out <= 6.0)
+    assert ctx.status() == 0

@@ -1,0 +1,86 @@
+"""Full SMC runs on the GPU (sharpy_smc_run) against analytic evidences and the oracle.
+
+ln Z criterion (reading of "within 2 combined standard errors"): R seeds per
+side, SE = std / sqrt(R), |mean_gpu - mean_ref| <= 2 sqrt(SE_gpu^2 + SE_ref^2).
+Seeds are fixed, so the outcome is deterministic.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2601_02336_gb300 import api, inputs
+from tests import gpu_helpers as G
+from tests import helpers
+from tests.test_oracle_sampler import gauss_lnz
+
+pytestmark = pytest.mark.gpu
+
+
+def _se(x):
+    x = np.asarray(x)
+    return x.std(ddof=1) / math.sqrt(len(x))
+
+
+def test_run_gaussian_analytic_evidence():
+    G.require_gpu()
+    mu, sig = [1.0, -2.0, 0.5], [0.5, 1.0, 0.3]
+    lo, hi = [-10.0] * 3, [10.0] * 3
+    ctx = api.Context(api.gaussmix_config(lo, hi, [0.0], [mu], [sig]))
+    truth = gauss_lnz(1.0, mu, sig, lo, hi)
+    lnzs = []
+    for seed in range(8):
+        lnz, th, lnl, rec = ctx.smc_run(1024, 0.5, 2, 5, 1, 0.5, key=700 + seed, precision="fp64")
+        lnzs.append(lnz)
+        cum = np.cumsum([r["dlnz"] for r in rec])
+        assert abs(cum[-1] - lnz) < 1e-9
+        assert rec[-1]["beta"] == 1.0
+        th = th.cpu().numpy()
+        assert np.allclose(th.mean(0), mu, atol=0.1)
+    assert abs(np.mean(lnzs) - truth) < 4 * _se(lnzs) + 0.02
+
+
+def test_run_bimodal_evidence():
+    G.require_gpu()
+    d = 3
+    lo, hi = [-5.0] * d, [5.0] * d
+    ctx = api.Context(api.gaussmix_config(lo, hi, [0.0, 0.0], [[1.0] * d, [-1.0] * d], [[0.3] * d, [0.3] * d]))
+    truth = math.log(2.0) - d * math.log(10.0)
+    lnzs = [ctx.smc_run(2048, 0.5, 2, 6, 1, 0.5, key=900 + s, precision="fp64")[0] for s in range(6)]
+    assert abs(np.mean(lnzs) - truth) < 4 * _se(lnzs) + 0.03
+
+
+def test_run_fp64_matches_oracle_per_seed():
+    """Same key: the GPU FP64 run and the oracle run take the same stages."""
+    G.require_gpu()
+    w = inputs.tiny()
+    ev, ctx, th_inj, _ = G.event_pair(w)
+    model = helpers.oracle_model(w)
+    close = 0
+    for seed in range(3):
+        ref = oracle.smc_run(model, ev, w.n_particles, w.alpha, w.n_mut, w.max_depth, w.metric, w.eps_scale,
+                             key=40 + seed)
+        got = ctx.smc_run(w.n_particles, w.alpha, w.n_mut, w.max_depth, w.metric, w.eps_scale, key=40 + seed,
+                          precision="fp64")
+        assert got[3][0]["beta"] == pytest.approx(ref[3][0]["beta"], rel=1e-10)
+        print("seed", seed, "gpu", got[0], len(got[3]), "oracle", ref[0], len(ref[3]),
+              [round(r["beta"], 6) for r in got[3]], [round(r["beta"], 6) for r in ref[3]])
+        if len(got[3]) == len(ref[3]) and abs(got[0] - ref[0]) < 1e-6:
+            close += 1
+    assert close >= 2
+
+
+def test_run_mixed_lnz_within_two_se():
+    G.require_gpu()
+    w = inputs.tiny()
+    ev, ctx, th_inj, _ = G.event_pair(w)
+    model = helpers.oracle_model(w)
+    R = 8
+    ref = [oracle.smc_run(model, ev, w.n_particles, w.alpha, w.n_mut, w.max_depth, w.metric, w.eps_scale,
+                          key=60 + s)[0] for s in range(R)]
+    got = [ctx.smc_run(w.n_particles, w.alpha, w.n_mut, w.max_depth, w.metric, w.eps_scale, key=80 + s,
+                       precision="mixed")[0] for s in range(R)]
+    assert abs(np.mean(got) - np.mean(ref)) <= 2.0 * math.sqrt(_se(got) ** 2 + _se(ref) ** 2), (got, ref)
+    assert ctx.status() == 0
