@@ -201,6 +201,25 @@ int sharpy_smc_reweight_resample(sharpy_ctx* ctx, int64_t n, double* theta, doub
    W is reported through ancestors = -1. */
 int sharpy_systematic_resample(int64_t n, const double* w, double u, int32_t* anc, sharpy_stream stream);
 
+/* Allocation-free variant of sharpy_systematic_resample, with the same
+   inputs, outputs and results. The paper has no counterpart: this is for
+   callers that cannot call cudaMalloc once they are running, for example a
+   sampler service that reserves its device memory up front and keeps its
+   budget fixed afterwards, or a caller that cannot accept the device-wide
+   synchronisation that allocating and freeing can cause. Its scratch (the
+   integer prefix sums and an invalid-weight flag) is a fixed device array
+   inside the library, sized for N <= 262144 (2 MiB), which every GPU that
+   loads the library keeps until the process exits. N above that returns
+   SHARPY_EINVAL; it allocates nothing (no cudaMalloc/cudaFree, no allocating
+   library call). The first call on a device, with that device current, looks
+   up the array's device address; make that first call before any stream
+   capture. All calls share the one array, which keeps the last call's
+   contents (the flag is cleared by each call): calls that overlap on the GPU
+   (other streams, other threads) race and must be serialised by the caller.
+   Synchronises `stream` (like sharpy_systematic_resample). */
+int sharpy_systematic_resample_static(int64_t n, const double* w, double u, int32_t* anc,
+                                      sharpy_stream stream);
+
 /* Reset the context's evidence accumulator (ln Z = 0, zero stages). */
 int sharpy_reset_evidence(sharpy_ctx* ctx, sharpy_stream stream);
 /* Sum of the evidence increments since the last reset (Sec. 3.1, Eq. 8) and

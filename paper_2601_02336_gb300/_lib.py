@@ -69,6 +69,7 @@ _SIGS = {
                                                C.c_double, C.c_double, _VP, _VP, _VP, _VP, _VP,
                                                _VP]),
     "sharpy_systematic_resample": (C.c_int, [C.c_int64, _VP, C.c_double, _VP, _VP]),
+    "sharpy_systematic_resample_static": (C.c_int, [C.c_int64, _VP, C.c_double, _VP, _VP]),
     "sharpy_reset_evidence": (C.c_int, [_CTX, _VP]),
     "sharpy_log_evidence": (C.c_int, [_CTX, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "sharpy_smc_run": (C.c_int, [_CTX, C.POINTER(SmcOptions), C.c_uint64, C.POINTER(C.c_double),
