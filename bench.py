@@ -33,11 +33,18 @@ sys.path.insert(0, ROOT)
 
 METRIC = "grad-lnL evals/s and SMC-NUTS run time, mixed vs FP64 on GB300, |ΔlnZ|≤2σ"
 UNIT = "evals/s"
-# Algorithmic work per active (bin, detector) of the mixed gradient sweep with 3
-# detectors: FP64 phase = 8 FMA per bin shared by the detectors + 1 FMA per
-# detector; FP32 = angle scale 1, carrier 6, moments 9 x 4 + 2 = 38 -> 45 FLOP.
-FP64_FLOP_PER_BIN_DET = 2.0 * (8.0 / 3.0 + 1.0)
-FP32_FLOP_PER_BIN_DET = 45.0
+# Algorithmic work per active (bin, detector) of the gradient sweep with 3
+# detectors (FMA = 2 FLOP). Carrier and moments (all paths): angle scale 1,
+# complex multiply 6, moments 9 x 4 + 2 -> 45 FLOP (FP32 in the mixed paths).
+# mixed: FP64 phase, 8 FMA per bin shared by 3 detectors + 1 FMA per detector.
+# split: FP32 phase, 8 split products per bin (~13.5 FLOP each) shared by 3
+#        detectors + ~15 FLOP per detector -> 51 FLOP, total 96 FP32 FLOP.
+# fp64: phase as mixed, carrier by sincospi (~30 FMA) and moments in FP64.
+WORK = {
+    "mixed": {"pipe": "fp64", "flop": 2.0 * (8.0 / 3.0 + 1.0), "fp32_flop": 45.0},
+    "split": {"pipe": "fp32", "flop": 96.0, "fp32_flop": 96.0},
+    "fp64": {"pipe": "fp64", "flop": 2.0 * (8.0 / 3.0 + 1.0) + 60.0 + 45.0, "fp32_flop": 0.0},
+}
 
 
 def _env_int(k, d):
@@ -154,7 +161,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sharpy", choices=["sharpy", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "split", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -240,20 +247,24 @@ def main():
     peaks = (C.c_double * 3)()
     lib().sharpy_probe_peaks(local, peaks)
     fp32_peak, fp64_peak = peaks[0], peaks[1]
-    fp64_ach = bins * FP64_FLOP_PER_BIN_DET / (nuts_ms * 1e-3) / 1e12
-    fp32_ach = bins * FP32_FLOP_PER_BIN_DET / (nuts_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": "nuts_kernel<MIXED,3>" if args.precision == "mixed" else
-                "nuts_kernel<FP64,3>", "achieved": fp64_ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": fp64_ach / fp64_peak if fp64_peak else None, "traffic": None,
-                "pipe": "fp64 (phase polynomial)", "peak_source": "measured FP64 FMA probe, this GPU",
+    wk = WORK[args.precision]
+    secs = nuts_ms * 1e-3
+    ach = bins * wk["flop"] / secs / 1e12
+    peak = fp64_peak if wk["pipe"] == "fp64" else fp32_peak
+    fp32_ach = bins * wk["fp32_flop"] / secs / 1e12
+    kname = {"mixed": "MIXED", "split": "MIXED_SPLIT", "fp64": "FP64"}[args.precision]
+    roofline = {"bound": "alu", "kernel": f"nuts_kernel<{kname},3>", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak if peak else None, "traffic": None,
+                "pipe": wk["pipe"], "flop_per_active_bin_det": wk["flop"],
+                "peak_source": f"measured {wk['pipe'].upper()} FMA probe on this GPU (sharpy_probe_peaks)",
                 "fp32_achieved": fp32_ach, "fp32_peak": fp32_peak,
-                "fp32_frac": fp32_ach / fp32_peak if fp32_peak else None,
+                "fp32_frac": fp32_ach / fp32_peak if fp32_peak else None, "fp64_peak": fp64_peak,
                 "nuts_share_of_step": nuts_ms / t_rank,
                 "active_bin_det_per_eval": bins / max(evals, 1)}
 
     # the other precision for the mixed-vs-FP64 comparison and |d lnZ| <= 2 sigma
     other = {}
-    if args.fp64_steps > 0 and args.precision == "mixed":
+    if args.fp64_steps > 0 and args.precision != "fp64":
         ev_o, t_o, lz_o = 0, 0.0, []
         for k in range(args.fp64_steps):
             flush.zero_()
@@ -315,7 +326,8 @@ def main():
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None,
-               "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+               "dtype": {"mixed": "f32+f64", "split": "f32 (f64 per particle)", "fp64": "f64"}[args.precision],
+               "data": "synthetic",
                "config": {"workload": "bbh11: 11-D aligned-spin TaylorF2, 3 detectors, 8 s at 1/8 Hz "
                                       "(8033 bins, 20-1024 Hz), 2048 particles, NUTS depth 6, alpha 0.5, "
                                       "2 transitions/stage, identity metric; one step = one full SMC run",

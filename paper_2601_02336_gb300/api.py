@@ -12,10 +12,10 @@ import numpy as np
 import torch
 
 from . import inputs
-from ._lib import (FP64, MIXED, MODEL_GAUSSMIX, MODEL_TAYLORF2, Config, Detector, NutsStats,
+from ._lib import (FP64, MIXED, MIXED_SPLIT, MODEL_GAUSSMIX, MODEL_TAYLORF2, Config, Detector, NutsStats,
                    SmcOptions, Stage, check, lib)
 
-PRECISION = {"fp64": FP64, "mixed": MIXED}
+PRECISION = {"fp64": FP64, "mixed": MIXED, "split": MIXED_SPLIT}
 STATS_DTYPE = np.dtype([("accept_sum", "<f8"), ("active_bins", "<f8"), ("depth_sum", "<i4"),
                         ("n_leapfrog", "<i4"), ("n_divergent", "<i4"), ("pad", "<i4")])
 

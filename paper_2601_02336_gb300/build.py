@@ -14,7 +14,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsharpy.so")
-UNITS = ["context.cu", "loglike.cu", "smc.cu", "nuts.cu", "run.cu", "probe.cu"]
+# (source, extra nvcc flags, object tag): nuts_inst.cu is compiled once per
+# (precision, detector count) so the persistent-kernel variants build in parallel.
+UNITS = [("context.cu", [], "context"), ("loglike.cu", [], "loglike"), ("smc.cu", [], "smc"),
+         ("nuts.cu", [], "nuts"), ("run.cu", [], "run"), ("probe.cu", [], "probe")] + [
+    ("nuts_inst.cu", [f"-DSHARPY_NUTS_PREC={p}", f"-DSHARPY_NUTS_NDET={d}"], f"nuts_p{p}_{d}")
+    for p in (0, 1, 2) for d in (1, 2, 3)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "-Xptxas", "-O3"]
 
@@ -27,7 +32,7 @@ def _nvcc():
 
 
 def _sources():
-    return [os.path.join(CSRC, u) for u in UNITS]
+    return sorted({os.path.join(CSRC, u[0]) for u in UNITS})
 
 
 def _deps():
@@ -49,9 +54,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     objs = []
 
-    def compile_one(src):
-        obj = os.path.join(OUT, os.path.basename(src) + f".{os.getpid()}.o")
-        cmd = [nvcc] + ARCH + FLAGS + ["-c", src, "-o", obj]
+    def compile_one(unit):
+        src, extra, tag = os.path.join(CSRC, unit[0]), unit[1], unit[2]
+        obj = os.path.join(OUT, f"{tag}.{os.getpid()}.o")
+        cmd = [nvcc] + ARCH + FLAGS + extra + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
@@ -59,8 +65,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
-        objs = list(ex.map(compile_one, _sources()))
+    with cf.ThreadPoolExecutor(max_workers=min(len(UNITS), max(2, os.cpu_count() or 2))) as ex:
+        objs = list(ex.map(compile_one, UNITS))
     tmp = LIB + f".tmp{os.getpid()}"
     cudalib = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")
     cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + \

@@ -42,6 +42,7 @@ struct DevDetector {
   int fixed_response;
   double fplus, fcross, delay;
   double D[3][3];  // detector tensor (x x^T - y y^T)/2
+  float Df[3][3];  // the same in FP32 (antenna patterns of the mixed path)
   double r[3];     // position [m]
 };
 
@@ -53,7 +54,8 @@ struct DevEvent {
   double dd;                 // <d|d> over all bins and detectors
   const double* f;           // [K] f_k
   const double* b64;         // [kNBasis][K] basis functions (FP64)
-  const float* b32;          // [kNBasis][K] basis functions (FP32)
+  const float* b32;          // [kNBasis][K] basis functions (FP32, = hi part)
+  const float* b32lo;        // [kNBasis][K] B - (double)hi (FP32 lo part)
   const double2* e64;        // [n_det][K] E = w conj(d) f^-7/6 (FP64)
   const float2* e32;         // [n_det][K] same, FP32
   const double* pref;        // [n_det][K] prefix sums of w f^-7/3

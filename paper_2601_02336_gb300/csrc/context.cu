@@ -35,11 +35,13 @@ static void free_event(sharpy_ctx* c) {
   cudaFree(c->d_f);
   cudaFree(c->d_b64);
   cudaFree(c->d_b32);
+  cudaFree(c->d_b32lo);
   cudaFree(c->d_e64);
   cudaFree(c->d_e32);
   cudaFree(c->d_pref);
   c->d_f = c->d_b64 = c->d_pref = nullptr;
   c->d_b32 = nullptr;
+  c->d_b32lo = nullptr;
   c->d_e64 = nullptr;
   c->d_e32 = nullptr;
   c->has_data = false;
@@ -61,7 +63,10 @@ static void detector_geometry(const sharpy_detector& in, DevDetector& out) {
     y[i] = -sa * north[i] + ca * east[i];
   }
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) out.D[i][j] = 0.5 * (x[i] * x[j] - y[i] * y[j]);
+    for (int j = 0; j < 3; ++j) {
+      out.D[i][j] = 0.5 * (x[i] * x[j] - y[i] * y[j]);
+      out.Df[i][j] = (float)out.D[i][j];
+    }
   out.r[0] = kEarthR * cl * co;
   out.r[1] = kEarthR * cl * so;
   out.r[2] = kEarthR * sl;
@@ -154,7 +159,7 @@ int sharpy_set_data(sharpy_ctx* c, int n_det, int64_t n_bins, double f_min, doub
   if (rc) return rc;
 
   std::vector<double> f(K), b64(kNBasis * K), e64(2 * n_det * K), pref(n_det * K);
-  std::vector<float> b32(kNBasis * K), e32(2 * n_det * K);
+  std::vector<float> b32(kNBasis * K), b32lo(kNBasis * K), e32(2 * n_det * K);
   for (int64_t k = 0; k < K; ++k) {
     double fk = f_min + (double)k * df;
     f[k] = fk;
@@ -164,6 +169,7 @@ int sharpy_set_data(sharpy_ctx* c, int n_det, int64_t n_bins, double f_min, doub
     for (int j = 0; j < kNBasis; ++j) {
       b64[j * K + k] = B[j];
       b32[j * K + k] = (float)B[j];
+      b32lo[j * K + k] = (float)(B[j] - (double)b32[j * K + k]);
     }
   }
   // <d|d> with a compensated sum; P_a prefix sums of w f^-7/3 (compensated).
@@ -195,6 +201,7 @@ int sharpy_set_data(sharpy_ctx* c, int n_det, int64_t n_bins, double f_min, doub
   bool ok = cudaMalloc(&c->d_f, K * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&c->d_b64, kNBasis * K * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&c->d_b32, kNBasis * K * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&c->d_b32lo, kNBasis * K * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&c->d_e64, n_det * K * sizeof(double2)) == cudaSuccess &&
             cudaMalloc(&c->d_e32, n_det * K * sizeof(float2)) == cudaSuccess &&
             cudaMalloc(&c->d_pref, n_det * K * sizeof(double)) == cudaSuccess;
@@ -205,6 +212,7 @@ int sharpy_set_data(sharpy_ctx* c, int n_det, int64_t n_bins, double f_min, doub
   ok = cudaMemcpy(c->d_f, f.data(), K * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(c->d_b64, b64.data(), b64.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(c->d_b32, b32.data(), b32.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
+       cudaMemcpy(c->d_b32lo, b32lo.data(), b32lo.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(c->d_e64, e64.data(), e64.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(c->d_e32, e32.data(), e32.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(c->d_pref, pref.data(), pref.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
@@ -221,6 +229,7 @@ int sharpy_set_data(sharpy_ctx* c, int n_det, int64_t n_bins, double f_min, doub
   ev.f = c->d_f;
   ev.b64 = c->d_b64;
   ev.b32 = c->d_b32;
+  ev.b32lo = c->d_b32lo;
   ev.e64 = c->d_e64;
   ev.e32 = c->d_e32;
   ev.pref = c->d_pref;

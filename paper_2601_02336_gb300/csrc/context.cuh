@@ -13,6 +13,7 @@ struct sharpy_ctx {
   double* d_f = nullptr;
   double* d_b64 = nullptr;
   float* d_b32 = nullptr;
+  float* d_b32lo = nullptr;
   double2* d_e64 = nullptr;
   float2* d_e32 = nullptr;
   double* d_pref = nullptr;

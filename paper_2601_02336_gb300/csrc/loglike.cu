@@ -23,7 +23,8 @@ loglike_kernel(DevModel m, DevEvent ev, int64_t n, const double* __restrict__ th
   using DT = typename std::conditional<PREC == SHARPY_FP64, double, float>::type;
   __shared__ SweepCoef sc[kWarps];
   __shared__ EpiCoef<DT> ec[kWarps];
-  __shared__ double mom[kWarps][NDET * kNMom * 2];
+  using MT = typename MomType<PREC>::type;
+  __shared__ MT mom[kWarps][NDET * kNMom * 2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t base = (int64_t)blockIdx.x * kWarps;
   const int D = m.n_dim;
@@ -32,7 +33,7 @@ loglike_kernel(DevModel m, DevEvent ev, int64_t n, const double* __restrict__ th
     if (p < n) {
       double th[kMaxDim];
       for (int i = 0; i < D; ++i) th[i] = theta[p * D + i];
-      prologue<DT, GRAD>(m, ev, th, sc[lane], ec[lane]);
+      prologue<DT, GRAD, PREC == SHARPY_MIXED_SPLIT>(m, ev, th, sc[lane], ec[lane]);
     } else {
       sc[lane].ok = 0;
       sc[lane].kisco = -1;
@@ -41,8 +42,8 @@ loglike_kernel(DevModel m, DevEvent ev, int64_t n, const double* __restrict__ th
   __syncthreads();
   {
     int64_t p = base + warp;
-    double* mw = mom[warp];
-    for (int i = lane; i < NDET * kNMom * 2; i += 32) mw[i] = 0.0;
+    MT* mw = mom[warp];
+    for (int i = lane; i < NDET * kNMom * 2; i += 32) mw[i] = MT(0);
     __syncwarp();
     if (p < n && sc[warp].ok) sweep<PREC, GRAD, NDET>(ev, sc[warp], mw);
   }
@@ -161,7 +162,8 @@ int sharpy_loglike_grad(sharpy_ctx* c, int64_t n, const double* theta, double* l
   int rc = check_ctx(c, true);
   if (rc) return rc;
   if (n < 0 || (n > 0 && (!theta || !lnl))) return SHARPY_EINVAL;
-  if (precision != SHARPY_FP64 && precision != SHARPY_MIXED) return SHARPY_EINVAL;
+  if (precision != SHARPY_FP64 && precision != SHARPY_MIXED && precision != SHARPY_MIXED_SPLIT)
+    return SHARPY_EINVAL;
   if (n == 0) return SHARPY_OK;
   if (n > ((int64_t)1 << 31) - 1) return SHARPY_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
@@ -172,8 +174,11 @@ int sharpy_loglike_grad(sharpy_ctx* c, int64_t n, const double* theta, double* l
     e = cudaGetLastError();
   } else if (precision == SHARPY_FP64) {
     e = grad ? launch_ll<SHARPY_FP64, true>(c, n, theta, lnl, grad, s) : launch_ll<SHARPY_FP64, false>(c, n, theta, lnl, grad, s);
-  } else {
+  } else if (precision == SHARPY_MIXED) {
     e = grad ? launch_ll<SHARPY_MIXED, true>(c, n, theta, lnl, grad, s) : launch_ll<SHARPY_MIXED, false>(c, n, theta, lnl, grad, s);
+  } else {
+    e = grad ? launch_ll<SHARPY_MIXED_SPLIT, true>(c, n, theta, lnl, grad, s)
+             : launch_ll<SHARPY_MIXED_SPLIT, false>(c, n, theta, lnl, grad, s);
   }
   return e == cudaSuccess ? SHARPY_OK : SHARPY_ECUDA;
 }

@@ -11,39 +11,60 @@
 // (Sec. 2, Eq. 2 with the Newtonian amplitude: <h|h> comes from the prefix
 // table P_a of w f^-7/3) and the exact gradient by the chain rule through the
 // moments (the adjoint of the sweep; the paper gets it by autodiff, Sec. 4).
+//
+// Precision (template DT): DT = double is the FP64 path. DT = float is the
+// mixed path: FP64 is kept for what the phase needs to ~1e-12 (the values of
+// alpha, c0 and the delays, k_ISCO) and for the ln L assembly; the antenna
+// patterns, the amplitude, every Jacobian entry and the gradient contraction
+// are FP32 (relative error ~1e-7, far inside the 1e-4 gradient tolerance).
 #pragma once
 #include "common.cuh"
 
 namespace sharpy {
 
-// Value (FP64) with derivatives along four directions (type DT).
+// Value with derivatives along four directions. The value is always FP64;
+// for DT = float an FP32 shadow of the value feeds the derivative arithmetic,
+// so derivatives never need FP64 operations or conversions.
 template <class DT>
-struct I4 {
+struct I4;
+
+template <>
+struct I4<double> {
   double v;
-  DT d[4];
-  __device__ __forceinline__ I4() {}
-  __device__ __forceinline__ I4(double x) : v(x) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) d[i] = DT(0);
-  }
-  __device__ __forceinline__ static I4 var(double x, int i) {
-    I4 r(x);
-    r.d[i] = DT(1);
-    return r;
-  }
+  double d[4];
+  __device__ __forceinline__ double f() const { return v; }
+  __device__ __forceinline__ void setf(double) {}
 };
+
+template <>
+struct I4<float> {
+  double v;
+  float vf;
+  float d[4];
+  __device__ __forceinline__ float f() const { return vf; }
+  __device__ __forceinline__ void setf(float x) { vf = x; }
+};
+
 template <class DT>
-__device__ __forceinline__ I4<DT> chain(const I4<DT>& x, double fv, double fp) {
+__device__ __forceinline__ I4<DT> iconst(double x) {
   I4<DT> r;
-  r.v = fv;
+  r.v = x;
+  r.setf((DT)x);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) r.d[i] = DT(fp) * x.d[i];
+  for (int i = 0; i < 4; ++i) r.d[i] = DT(0);
+  return r;
+}
+template <class DT>
+__device__ __forceinline__ I4<DT> ivar(double x, int k) {
+  I4<DT> r = iconst<DT>(x);
+  r.d[k] = DT(1);
   return r;
 }
 template <class DT>
 __device__ __forceinline__ I4<DT> operator+(const I4<DT>& a, const I4<DT>& b) {
   I4<DT> r;
   r.v = a.v + b.v;
+  r.setf(a.f() + b.f());
 #pragma unroll
   for (int i = 0; i < 4; ++i) r.d[i] = a.d[i] + b.d[i];
   return r;
@@ -52,6 +73,7 @@ template <class DT>
 __device__ __forceinline__ I4<DT> operator-(const I4<DT>& a, const I4<DT>& b) {
   I4<DT> r;
   r.v = a.v - b.v;
+  r.setf(a.f() - b.f());
 #pragma unroll
   for (int i = 0; i < 4; ++i) r.d[i] = a.d[i] - b.d[i];
   return r;
@@ -60,37 +82,58 @@ template <class DT>
 __device__ __forceinline__ I4<DT> operator*(const I4<DT>& a, const I4<DT>& b) {
   I4<DT> r;
   r.v = a.v * b.v;
+  r.setf(a.f() * b.f());
 #pragma unroll
-  for (int i = 0; i < 4; ++i) r.d[i] = a.d[i] * DT(b.v) + DT(a.v) * b.d[i];
+  for (int i = 0; i < 4; ++i) r.d[i] = a.d[i] * b.f() + a.f() * b.d[i];
   return r;
 }
 template <class DT>
 __device__ __forceinline__ I4<DT> operator*(double s, const I4<DT>& a) {
   I4<DT> r;
   r.v = s * a.v;
+  r.setf((DT)s * a.f());
 #pragma unroll
-  for (int i = 0; i < 4; ++i) r.d[i] = DT(s) * a.d[i];
+  for (int i = 0; i < 4; ++i) r.d[i] = (DT)s * a.d[i];
   return r;
 }
 template <class DT>
 __device__ __forceinline__ I4<DT> operator+(double s, const I4<DT>& a) {
   I4<DT> r = a;
   r.v = s + a.v;
+  r.setf((DT)s + a.f());
   return r;
 }
+// 1 / a
 template <class DT>
 __device__ __forceinline__ I4<DT> recip(const I4<DT>& a) {
-  double iv = 1.0 / a.v;
-  return chain(a, iv, -iv * iv);
+  I4<DT> r;
+  r.v = 1.0 / a.v;
+  r.setf((DT)r.v);
+  const DT g = -r.f() * r.f();
+#pragma unroll
+  for (int i = 0; i < 4; ++i) r.d[i] = g * a.d[i];
+  return r;
 }
-template <class DT>
-__device__ __forceinline__ I4<DT> ipow(const I4<DT>& a, double p) {  // a^p, a > 0
-  double y = pow(a.v, p);
-  return chain(a, y, p * y / a.v);
-}
+// ln a
 template <class DT>
 __device__ __forceinline__ I4<DT> ilog(const I4<DT>& a) {
-  return chain(a, log(a.v), 1.0 / a.v);
+  I4<DT> r;
+  r.v = log(a.v);
+  r.setf((DT)r.v);
+  const DT g = DT(1) / a.f();
+#pragma unroll
+  for (int i = 0; i < 4; ++i) r.d[i] = g * a.d[i];
+  return r;
+}
+// e^a
+template <class DT>
+__device__ __forceinline__ I4<DT> iexp(const I4<DT>& a) {
+  I4<DT> r;
+  r.v = exp(a.v);
+  r.setf((DT)r.v);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) r.d[i] = r.f() * a.d[i];
+  return r;
 }
 
 // Everything the sweep needs for one particle (kept in shared memory).
@@ -98,20 +141,29 @@ struct SweepCoef {
   double alpha[kNPn];   // phase basis coefficients [turns]
   double c0;            // constant phase [turns]
   double tau[kMaxDet];  // t_c + delay_a [s]
+  // split single-precision copies (SHARPY_MIXED_SPLIT): x = hi + lo to ~48 bits
+  float ahi[kNPn], alo[kNPn];
+  float thi[kMaxDet], tlo[kMaxDet];
+  float c0f;            // c0 reduced to [-1/2, 1/2] turns
   int kisco;            // last bin with f_k <= f_ISCO (-1: none)
   int ok;               // 0 if the parameters are outside the model's domain
 };
+
+__device__ __forceinline__ void split2(double x, float* hi, float* lo) {
+  *hi = (float)x;
+  *lo = (float)(x - (double)*hi);
+}
 
 // Everything the epilogue needs beyond the moments.
 template <class DT>
 struct EpiCoef {
   double A0;
-  double cre[kMaxDet], cim[kMaxDet];
-  DT dalpha[kNPn][4];           // d alpha_j / d(Mc, q, chi1, chi2)
+  DT cre[kMaxDet], cim[kMaxDet];          // C_a
+  DT dalpha[kNPn][4];                     // d alpha_j / d(Mc, q, chi1, chi2)
   DT dc0[4];
-  DT dA0_mc, dA0_dl;
+  DT rel_mc, rel_dl;                      // d ln A0 / d Mc, d ln A0 / d d_L
   DT dcre[kMaxDet][4], dcim[kMaxDet][4];  // d C_a / d(cos i, psi, ra, sin dec)
-  DT dtau[kMaxDet][2];                     // d tau_a / d(ra, sin dec)
+  DT dtau[kMaxDet][2];                    // d tau_a / d(ra, sin dec)
 };
 
 // Map the free parameters of one particle onto the eleven physical ones.
@@ -122,62 +174,71 @@ __device__ __forceinline__ void to_physical(const DevModel& m, const double* th,
 }
 
 // TaylorF2 phase coefficients in turns and their Jacobian w.r.t. (Mc, q, chi1, chi2).
+// Transcendentals in FP64: ln eta, ln Mc and one exponential (u).
 template <class DT>
-__device__ void pn_coefficients(const double* ph, I4<DT>* alpha, I4<DT>& cpn, I4<DT>& mtot) {
-  I4<DT> mc = I4<DT>::var(ph[SHARPY_MC], 0);
-  I4<DT> q = I4<DT>::var(ph[SHARPY_Q], 1);
-  I4<DT> c1 = I4<DT>::var(ph[SHARPY_CHI1], 2);
-  I4<DT> c2 = I4<DT>::var(ph[SHARPY_CHI2], 3);
-  I4<DT> onepq = 1.0 + q;
-  I4<DT> m1 = recip(onepq);        // m1 / M
-  I4<DT> m2 = q * m1;              // m2 / M
-  I4<DT> eta = m1 * m2;
-  I4<DT> delta = m1 - m2;
-  mtot = mc * ipow(eta, -0.6);
-  I4<DT> u = ipow((kPi * kTsun) * mtot, 1.0 / 3.0);   // v = u f^(1/3)
-  I4<DT> lnu = ilog(u);
-  I4<DT> chis = 0.5 * (c1 + c2);
-  I4<DT> chia = 0.5 * (c1 - c2);
-  I4<DT> eta2 = eta * eta;
+__device__ void pn_coefficients(const double* ph, I4<DT>* alpha, I4<DT>& cpn, double& mtot) {
+  const I4<DT> mc = ivar<DT>(ph[SHARPY_MC], 0);
+  const I4<DT> q = ivar<DT>(ph[SHARPY_Q], 1);
+  const I4<DT> c1 = ivar<DT>(ph[SHARPY_CHI1], 2);
+  const I4<DT> c2 = ivar<DT>(ph[SHARPY_CHI2], 3);
+  const I4<DT> onepq = 1.0 + q;
+  const I4<DT> m1 = recip(onepq);  // m1 / M
+  const I4<DT> m2 = q * m1;        // m2 / M
+  const I4<DT> eta = m1 * m2;
+  const I4<DT> delta = m1 - m2;
+  // ln u = (ln(pi Tsun) + ln Mc - 3/5 ln eta) / 3, v = u f^(1/3), M = u^3 / (pi Tsun)
+  const I4<DT> lnu = (1.0 / 3.0) * ((-11.076356701842613) + (ilog(mc) + (-0.6) * ilog(eta)));
+  const I4<DT> u = iexp(lnu);
+  mtot = u.v * u.v * u.v / (kPi * kTsun);
+  const I4<DT> chis = 0.5 * (c1 + c2);
+  const I4<DT> chia = 0.5 * (c1 - c2);
+  const I4<DT> eta2 = eta * eta;
   // spin-orbit (1.5PN, 2.5PN) and spin-spin (2PN) combinations
-  I4<DT> beta = ((113.0 / 12.0) + (-19.0 / 3.0) * eta) * chis + (113.0 / 12.0) * (delta * chia);
-  I4<DT> gam = ((732985.0 / 2268.0) + (-24260.0 / 81.0) * eta + (-340.0 / 9.0) * eta2) * chis +
-               ((732985.0 / 2268.0) + (140.0 / 9.0) * eta) * (delta * chia);
-  I4<DT> sig = (79.0 / 8.0) * (eta * (c1 * c2)) + (81.0 / 16.0) * (m1 * m1 * c1 * c1 + m2 * m2 * c2 * c2);
-  I4<DT> p2 = (3715.0 / 756.0) + (55.0 / 9.0) * eta;
-  I4<DT> p3 = (-16.0 * kPi) + 4.0 * beta;
-  I4<DT> p4 = (15293365.0 / 508032.0) + (27145.0 / 504.0) * eta + (3085.0 / 72.0) * eta2 + (-10.0) * sig;
-  I4<DT> p5 = (kPi * 38645.0 / 756.0) + (-kPi * 65.0 / 9.0) * eta - gam;
-  I4<DT> p6 = (11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * kPi * kPi - 6848.0 / 21.0 * kEulerGamma) +
-              (-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * kPi * kPi) * eta + (76055.0 / 1728.0) * eta2 +
-              (-127825.0 / 1296.0) * (eta2 * eta);
-  I4<DT> p7 = kPi * ((77096675.0 / 254016.0) + (378515.0 / 1512.0) * eta + (-74045.0 / 756.0) * eta2);
-  I4<DT> nt = (3.0 / (128.0 * kTwoPi)) * recip(eta);   // 3 / (128 eta) in turns
-  I4<DT> ui = recip(u);
-  I4<DT> ui2 = ui * ui;
-  I4<DT> ui3 = ui2 * ui;
-  alpha[0] = nt * (ui3 * ui2);                        // x^5
-  alpha[1] = nt * (p2 * ui3);                         // x^3
-  alpha[2] = nt * (p3 * ui2);                         // x^2
-  alpha[3] = nt * (p4 * ui);                          // x
-  alpha[4] = nt * p5;                                 // ln f
-  I4<DT> l4u = ilog(4.0 * u);
-  alpha[5] = nt * (u * (p6 + (-6848.0 / 21.0) * l4u));  // y
-  alpha[6] = (-6848.0 / 63.0) * (nt * u);               // y ln f
-  alpha[7] = nt * (p7 * (u * u));                       // y^2
+  const I4<DT> beta = ((113.0 / 12.0) + (-19.0 / 3.0) * eta) * chis + (113.0 / 12.0) * (delta * chia);
+  const I4<DT> gam = ((732985.0 / 2268.0) + ((-24260.0 / 81.0) * eta + (-340.0 / 9.0) * eta2)) * chis +
+                     ((732985.0 / 2268.0) + (140.0 / 9.0) * eta) * (delta * chia);
+  const I4<DT> sig =
+      (79.0 / 8.0) * (eta * (c1 * c2)) + (81.0 / 16.0) * (m1 * m1 * c1 * c1 + m2 * m2 * c2 * c2);
+  const I4<DT> p2 = (3715.0 / 756.0) + (55.0 / 9.0) * eta;
+  const I4<DT> p3 = (-16.0 * kPi) + 4.0 * beta;
+  const I4<DT> p4 =
+      (15293365.0 / 508032.0) + ((27145.0 / 504.0) * eta + (3085.0 / 72.0) * eta2 + (-10.0) * sig);
+  const I4<DT> p5 = (kPi * 38645.0 / 756.0) + ((-kPi * 65.0 / 9.0) * eta - gam);
+  const I4<DT> p6 =
+      (11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * kPi * kPi - 6848.0 / 21.0 * kEulerGamma) +
+      ((-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * kPi * kPi) * eta + (76055.0 / 1728.0) * eta2 +
+       (-127825.0 / 1296.0) * (eta2 * eta));
+  const I4<DT> p7 = kPi * ((77096675.0 / 254016.0) + ((378515.0 / 1512.0) * eta + (-74045.0 / 756.0) * eta2));
+  // 3 / (128 eta) in turns; 1/eta = (1+q)^2 / q
+  const I4<DT> nt = (3.0 / (128.0 * kTwoPi)) * (onepq * onepq * recip(q));
+  const I4<DT> ui = recip(u);
+  const I4<DT> ui2 = ui * ui;
+  const I4<DT> ui3 = ui2 * ui;
+  alpha[0] = nt * (ui3 * ui2);  // x^5
+  alpha[1] = nt * (p2 * ui3);   // x^3
+  alpha[2] = nt * (p3 * ui2);   // x^2
+  alpha[3] = nt * (p4 * ui);    // x
+  alpha[4] = nt * p5;           // ln f
+  // ln(4u) = ln 4 + ln u
+  alpha[5] = nt * (u * (p6 + (-6848.0 / 21.0) * (1.3862943611198906 + lnu)));  // y
+  alpha[6] = (-6848.0 / 63.0) * (nt * u);                                       // y ln f
+  alpha[7] = nt * (p7 * (u * u));                                               // y^2
   // constant: p5 (1 + 3 ln(u / v_lso)), v_lso = 6^(-1/2)
   cpn = nt * (p5 * ((1.0 + 1.5 * 1.791759469228055) + 3.0 * lnu));
 }
 
-// Antenna pattern, delay and their derivatives w.r.t. (psi, ra, sin dec).
+// Antenna pattern (type AT), delay (FP64) and their derivatives w.r.t. (psi, ra, sin dec).
+template <class AT>
 struct Antenna {
-  double fp, fc, dt;
-  double dfp[3], dfc[3];  // d/d(psi, ra, sin dec)
-  double ddt[2];          // d/d(ra, sin dec)
+  AT fp, fc;
+  double dt;
+  AT dfp[3], dfc[3];  // d/d(psi, ra, sin dec)
+  AT ddt[2];          // d delay / d(ra, sin dec)
 };
 
-__device__ __forceinline__ double quad(const double D[3][3], const double* a, const double* b) {
-  double s = 0.0;
+template <class AT>
+__device__ __forceinline__ AT quad(const AT (*D)[3], const AT* a, const AT* b) {
+  AT s = AT(0);
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -185,45 +246,50 @@ __device__ __forceinline__ double quad(const double D[3][3], const double* a, co
   return s;
 }
 
-static __device__ void antenna(const DevDetector& det, double ra, double sdec, double psi, Antenna& out) {
+__device__ __forceinline__ void sincos2psi(double psi, double* s2, double* c2) { sincos(2.0 * psi, s2, c2); }
+__device__ __forceinline__ void sincos2psi(double psi, float* s2, float* c2) { sincosf(2.0f * (float)psi, s2, c2); }
+__device__ __forceinline__ const double (*det_tensor(const DevDetector& det, double))[3] { return det.D; }
+__device__ __forceinline__ const float (*det_tensor(const DevDetector& det, float))[3] { return det.Df; }
+
+template <class AT>
+static __device__ void antenna(const DevDetector& det, double sa, double ca, double cd, double sdec, AT s2, AT c2,
+                               Antenna<AT>& out) {
   if (det.fixed_response) {
-    out.fp = det.fplus;
-    out.fc = det.fcross;
+    out.fp = (AT)det.fplus;
+    out.fc = (AT)det.fcross;
     out.dt = det.delay;
-    for (int i = 0; i < 3; ++i) out.dfp[i] = out.dfc[i] = 0.0;
-    out.ddt[0] = out.ddt[1] = 0.0;
+    for (int i = 0; i < 3; ++i) out.dfp[i] = out.dfc[i] = AT(0);
+    out.ddt[0] = out.ddt[1] = AT(0);
     return;
   }
-  double sa, ca, s2, c2;
-  sincos(ra, &sa, &ca);
-  sincos(2.0 * psi, &s2, &c2);
-  double cd = sqrt(fmax(1.0 - sdec * sdec, 0.0));
-  double n[3] = {cd * ca, cd * sa, sdec};
-  double p[3] = {sa, -ca, 0.0};
-  double q[3] = {sdec * ca, sdec * sa, -cd};
-  double dp_ra[3] = {ca, sa, 0.0};
-  double dq_ra[3] = {-sdec * sa, sdec * ca, 0.0};
-  double dq_sd[3] = {ca, sa, sdec / cd};
-  double dn_ra[3] = {-cd * sa, cd * ca, 0.0};
-  double dn_sd[3] = {-sdec * ca / cd, -sdec * sa / cd, 1.0};
-  double fp0 = quad(det.D, p, p) - quad(det.D, q, q);
-  double fc0 = 2.0 * quad(det.D, p, q);
-  double dfp0_ra = 2.0 * quad(det.D, p, dp_ra) - 2.0 * quad(det.D, q, dq_ra);
-  double dfc0_ra = 2.0 * (quad(det.D, dp_ra, q) + quad(det.D, p, dq_ra));
-  double dfp0_sd = -2.0 * quad(det.D, q, dq_sd);
-  double dfc0_sd = 2.0 * quad(det.D, p, dq_sd);
+  const double* r = det.r;
+  // geocentric delay in FP64 (it multiplies frequencies up to kHz in the phase)
+  out.dt = -(r[0] * (cd * ca) + r[1] * (cd * sa) + r[2] * sdec) * (1.0 / kClight);
+  const AT a_s = (AT)sa, a_c = (AT)ca, a_d = (AT)cd, a_z = (AT)sdec;
+  const AT p[3] = {a_s, -a_c, AT(0)};
+  const AT q[3] = {a_z * a_c, a_z * a_s, -a_d};
+  const AT dp_ra[3] = {a_c, a_s, AT(0)};
+  const AT dq_ra[3] = {-a_z * a_s, a_z * a_c, AT(0)};
+  const AT dq_sd[3] = {a_c, a_s, a_z / a_d};
+  const AT (*D)[3] = det_tensor(det, AT(0));
+  const AT fp0 = quad<AT>(D, p, p) - quad<AT>(D, q, q);
+  const AT fc0 = AT(2) * quad<AT>(D, p, q);
+  const AT dfp0_ra = AT(2) * (quad<AT>(D, p, dp_ra) - quad<AT>(D, q, dq_ra));
+  const AT dfc0_ra = AT(2) * (quad<AT>(D, dp_ra, q) + quad<AT>(D, p, dq_ra));
+  const AT dfp0_sd = AT(-2) * quad<AT>(D, q, dq_sd);
+  const AT dfc0_sd = AT(2) * quad<AT>(D, p, dq_sd);
   out.fp = c2 * fp0 + s2 * fc0;
   out.fc = -s2 * fp0 + c2 * fc0;
-  out.dfp[0] = 2.0 * out.fc;
-  out.dfc[0] = -2.0 * out.fp;
+  out.dfp[0] = AT(2) * out.fc;
+  out.dfc[0] = AT(-2) * out.fp;
   out.dfp[1] = c2 * dfp0_ra + s2 * dfc0_ra;
   out.dfc[1] = -s2 * dfp0_ra + c2 * dfc0_ra;
   out.dfp[2] = c2 * dfp0_sd + s2 * dfc0_sd;
   out.dfc[2] = -s2 * dfp0_sd + c2 * dfc0_sd;
-  const double* r = det.r;
-  out.dt = -(r[0] * n[0] + r[1] * n[1] + r[2] * n[2]) / kClight;
-  out.ddt[0] = -(r[0] * dn_ra[0] + r[1] * dn_ra[1] + r[2] * dn_ra[2]) / kClight;
-  out.ddt[1] = -(r[0] * dn_sd[0] + r[1] * dn_sd[1] + r[2] * dn_sd[2]) / kClight;
+  const AT rc[3] = {(AT)(r[0] / kClight), (AT)(r[1] / kClight), (AT)(r[2] / kClight)};
+  // d n / d ra = (-cd sa, cd ca, 0); d n / d sin dec = (-sdec ca / cd, -sdec sa / cd, 1)
+  out.ddt[0] = -(rc[0] * (-a_d * a_s) + rc[1] * (a_d * a_c));
+  out.ddt[1] = -(rc[0] * (-a_z * a_c / a_d) + rc[1] * (-a_z * a_s / a_d) + rc[2]);
 }
 
 // Last bin with f_k <= f_isco, using the staged frequency table.
@@ -237,18 +303,21 @@ __device__ __forceinline__ int isco_bin(const DevEvent& ev, double fisco) {
 }
 
 // theta (free dims) -> sweep and epilogue coefficients.
-template <class DT, bool GRAD>
+template <class DT, bool GRAD, bool SPLIT = false>
 __device__ void prologue(const DevModel& m, const DevEvent& ev, const double* th, SweepCoef& sc,
                          EpiCoef<DT>& ec) {
   double ph[SHARPY_NPHYS];
   to_physical(m, th, ph);
   sc.ok = (ph[SHARPY_MC] > 0.0 && ph[SHARPY_Q] > 0.0 && ph[SHARPY_DL] > 0.0 && fabs(ph[SHARPY_SINDEC]) <= 1.0 &&
-           fabs(ph[SHARPY_COSI]) <= 1.0) ? 1 : 0;
+           fabs(ph[SHARPY_COSI]) <= 1.0)
+              ? 1
+              : 0;
   if (!sc.ok) {
     sc.kisco = -1;
     return;
   }
-  I4<DT> alpha[kNPn], cpn, mtot;
+  I4<DT> alpha[kNPn], cpn;
+  double mtot;
   pn_coefficients<DT>(ph, alpha, cpn, mtot);
 #pragma unroll
   for (int j = 0; j < kNPn; ++j) {
@@ -257,93 +326,118 @@ __device__ void prologue(const DevModel& m, const DevEvent& ev, const double* th
 #pragma unroll
       for (int i = 0; i < 4; ++i) ec.dalpha[j][i] = alpha[j].d[i];
   }
-  sc.c0 = cpn.v - ph[SHARPY_PHIC] / kTwoPi - 0.125;
+  sc.c0 = cpn.v - ph[SHARPY_PHIC] * (1.0 / kTwoPi) - 0.125;
   if (GRAD)
 #pragma unroll
     for (int i = 0; i < 4; ++i) ec.dc0[i] = cpn.d[i];
-  double fisco = 1.0 / (14.696938456699069 * kPi * kTsun * mtot.v);  // 6^(3/2) pi M
+  const double fisco = 1.0 / (14.696938456699069 * kPi * kTsun * mtot);  // 6^(3/2) pi M
   sc.kisco = isco_bin(ev, fisco);
 
   // Newtonian amplitude of an optimally oriented source: sqrt(5/24) pi^(-2/3) (T Mc)^(5/6) / D
-  double mc = ph[SHARPY_MC], dl = ph[SHARPY_DL];
-  ec.A0 = 0.45643546458763845 * 0.46619407703541166 * pow(kTsun * mc, 5.0 / 6.0) / (dl * kMpcSec);
+  const DT mc = (DT)ph[SHARPY_MC], dl = (DT)ph[SHARPY_DL];
+  ec.A0 = (double)((DT)(0.45643546458763845 * 0.46619407703541166) * pow((DT)kTsun * mc, DT(5.0 / 6.0)) /
+                   (dl * (DT)kMpcSec));
   if (GRAD) {
-    ec.dA0_mc = DT(5.0 / 6.0 * ec.A0 / mc);
-    ec.dA0_dl = DT(-ec.A0 / dl);
+    ec.rel_mc = DT(5.0 / 6.0) / mc;
+    ec.rel_dl = DT(-1) / dl;
   }
-  double ci = ph[SHARPY_COSI];
+  const DT ci = (DT)ph[SHARPY_COSI];
+  double sa = 0.0, ca = 1.0, cd = 1.0;
+  DT s2 = DT(0), c2 = DT(1);
+  bool any_sky = false;
+  for (int a = 0; a < ev.n_det; ++a) any_sky = any_sky || !ev.det[a].fixed_response;
+  if (any_sky) {
+    sincos(ph[SHARPY_RA], &sa, &ca);
+    cd = sqrt(fmax(1.0 - ph[SHARPY_SINDEC] * ph[SHARPY_SINDEC], 0.0));
+    sincos2psi(ph[SHARPY_PSI], &s2, &c2);
+  }
   for (int a = 0; a < ev.n_det; ++a) {
-    Antenna an;
-    antenna(ev.det[a], ph[SHARPY_RA], ph[SHARPY_SINDEC], ph[SHARPY_PSI], an);
+    Antenna<DT> an;
+    antenna<DT>(ev.det[a], sa, ca, cd, ph[SHARPY_SINDEC], s2, c2, an);
     sc.tau[a] = ph[SHARPY_TC] + an.dt;
-    double hp = 0.5 * (1.0 + ci * ci);
+    const DT hp = DT(0.5) * (DT(1) + ci * ci);
     ec.cre[a] = an.fp * hp;
     ec.cim[a] = -an.fc * ci;
     if (GRAD) {
-      ec.dcre[a][0] = DT(an.fp * ci);
-      ec.dcim[a][0] = DT(-an.fc);
+      ec.dcre[a][0] = an.fp * ci;
+      ec.dcim[a][0] = -an.fc;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        ec.dcre[a][k + 1] = DT(an.dfp[k] * hp);
-        ec.dcim[a][k + 1] = DT(-an.dfc[k] * ci);
+        ec.dcre[a][k + 1] = an.dfp[k] * hp;
+        ec.dcim[a][k + 1] = -an.dfc[k] * ci;
       }
-      ec.dtau[a][0] = DT(an.ddt[0]);
-      ec.dtau[a][1] = DT(an.ddt[1]);
+      ec.dtau[a][0] = an.ddt[0];
+      ec.dtau[a][1] = an.ddt[1];
     }
+  }
+  if (SPLIT) {
+#pragma unroll
+    for (int j = 0; j < kNPn; ++j) split2(sc.alpha[j], &sc.ahi[j], &sc.alo[j]);
+    for (int a = 0; a < ev.n_det; ++a) split2(sc.tau[a], &sc.thi[a], &sc.tlo[a]);
+    sc.c0f = (float)(sc.c0 - rint(sc.c0));
   }
 }
 
 // Moments layout: mom[a][j][re/im], j = 0..8 basis (8 = f), j = 9 plain sum Z.
 constexpr int kNMom = kNBasis + 1;
 
-// ln L and d lnL / d(physical parameters) from the moments. The arithmetic is
-// FP64 throughout (the moments and prefix sums span ~1e-22..1e43, beyond FP32
-// range); DT only sets the storage precision of the Jacobian.
-template <class DT, bool GRAD>
-__device__ void epilogue(const DevEvent& ev, const SweepCoef& sc, const EpiCoef<DT>& ec, const double* mom,
-                         double* lnl, double* gph) {
+// ln L (FP64) and d lnL / d(physical parameters) from the moments.
+// The gradient is contracted on the amplitude-scaled moments A0 Z, A0 Y_j and
+// the scaled prefix sum A0^2 P, which are O(SNR^2) and fit FP32 (the raw moments
+// and prefix sums span ~1e-22..1e43).
+template <class DT, bool GRAD, class MT>
+__device__ void epilogue(const DevEvent& ev, const SweepCoef& sc, const EpiCoef<DT>& ec, const MT* mom, double* lnl,
+                         double* gph) {
   double acc = -0.5 * ev.dd;
-  double g[SHARPY_NPHYS];
+  DT g[SHARPY_NPHYS];
 #pragma unroll
-  for (int i = 0; i < SHARPY_NPHYS; ++i) g[i] = 0.0;
+  for (int i = 0; i < SHARPY_NPHYS; ++i) g[i] = DT(0);
+  const DT a0 = (DT)ec.A0;
   for (int a = 0; a < ev.n_det; ++a) {
-    const double* M = mom + a * kNMom * 2;
+    const MT* M = mom + a * kNMom * 2;
     const double P = sc.kisco >= 0 ? ev.pref[(int64_t)a * ev.n_bins + sc.kisco] : 0.0;
-    const double Gr = ec.A0 * ec.cre[a], Gi = ec.A0 * ec.cim[a];
-    const double Zr = M[2 * 9], Zi = M[2 * 9 + 1];
-    acc += (Gr * Zr - Gi * Zi) - 0.5 * (Gr * Gr + Gi * Gi) * P;
+    const double Gr = ec.A0 * (double)ec.cre[a], Gi = ec.A0 * (double)ec.cim[a];
+    acc += (Gr * (double)M[18] - Gi * (double)M[19]) - 0.5 * (Gr * Gr + Gi * Gi) * P;
     if (!GRAD) continue;
-    const double tp = kTwoPi;
-    // Im(G X) for a phase-derivative moment X
-    auto imgx = [&](double xr, double xi) { return Gr * xi + Gi * xr; };
-    // Re(dG Z) - Re(conj(G) dG) P for an amplitude/response derivative dG
-    auto amp = [&](double dr, double di) { return (dr * Zr - di * Zi) - (Gr * dr + Gi * di) * P; };
+    const DT cr = ec.cre[a], ci = ec.cim[a];
+    const DT ps = (DT)(ec.A0 * ec.A0 * P);             // A0^2 P
+    const DT zr = a0 * (DT)M[18], zi = a0 * (DT)M[19];  // A0 Z
+    const DT tp = DT(kTwoPi);
+    // Im(C X) for a scaled phase-derivative moment X
+    auto imcx = [&](DT xr, DT xi) { return cr * xi + ci * xr; };
+    // Re(dC A0 Z) - Re(conj(C) dC) A0^2 P for a response derivative dC
+    auto resp = [&](DT dr, DT di) { return (dr * zr - di * zi) - (cr * dr + ci * di) * ps; };
+    DT yr[kNPn], yi[kNPn];
+#pragma unroll
+    for (int j = 0; j < kNPn; ++j) {
+      yr[j] = a0 * (DT)M[2 * j];
+      yi[j] = a0 * (DT)M[2 * j + 1];
+    }
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
-      double xr = (double)ec.dc0[p] * Zr, xi = (double)ec.dc0[p] * Zi;
+      DT xr = ec.dc0[p] * zr, xi = ec.dc0[p] * zi;
 #pragma unroll
       for (int j = 0; j < kNPn; ++j) {
-        xr += (double)ec.dalpha[j][p] * M[2 * j];
-        xi += (double)ec.dalpha[j][p] * M[2 * j + 1];
+        xr += ec.dalpha[j][p] * yr[j];
+        xi += ec.dalpha[j][p] * yi[j];
       }
-      g[p] += tp * imgx(xr, xi);
+      g[p] += tp * imcx(xr, xi);
     }
-    const double cr = ec.cre[a], ci = ec.cim[a], A0 = ec.A0;
-    g[SHARPY_MC] += amp((double)ec.dA0_mc * cr, (double)ec.dA0_mc * ci);
-    g[SHARPY_DL] += amp((double)ec.dA0_dl * cr, (double)ec.dA0_dl * ci);
-    g[SHARPY_COSI] += amp(A0 * (double)ec.dcre[a][0], A0 * (double)ec.dcim[a][0]);
-    g[SHARPY_PSI] += amp(A0 * (double)ec.dcre[a][1], A0 * (double)ec.dcim[a][1]);
-    const double yfr = M[2 * 8], yfi = M[2 * 8 + 1];
-    const double dt0 = ec.dtau[a][0], dt1 = ec.dtau[a][1];
-    g[SHARPY_RA] += amp(A0 * (double)ec.dcre[a][2], A0 * (double)ec.dcim[a][2]) + tp * imgx(dt0 * yfr, dt0 * yfi);
-    g[SHARPY_SINDEC] += amp(A0 * (double)ec.dcre[a][3], A0 * (double)ec.dcim[a][3]) + tp * imgx(dt1 * yfr, dt1 * yfi);
-    g[SHARPY_TC] += tp * imgx(yfr, yfi);
-    g[SHARPY_PHIC] += -imgx(Zr, Zi);
+    const DT amp = (cr * zr - ci * zi) - (cr * cr + ci * ci) * ps;  // d/d ln A0
+    g[SHARPY_MC] += ec.rel_mc * amp;
+    g[SHARPY_DL] += ec.rel_dl * amp;
+    g[SHARPY_COSI] += resp(ec.dcre[a][0], ec.dcim[a][0]);
+    g[SHARPY_PSI] += resp(ec.dcre[a][1], ec.dcim[a][1]);
+    const DT yfr = a0 * (DT)M[16], yfi = a0 * (DT)M[17];
+    g[SHARPY_RA] += resp(ec.dcre[a][2], ec.dcim[a][2]) + tp * imcx(ec.dtau[a][0] * yfr, ec.dtau[a][0] * yfi);
+    g[SHARPY_SINDEC] += resp(ec.dcre[a][3], ec.dcim[a][3]) + tp * imcx(ec.dtau[a][1] * yfr, ec.dtau[a][1] * yfi);
+    g[SHARPY_TC] += tp * imcx(yfr, yfi);
+    g[SHARPY_PHIC] += -imcx(zr, zi);
   }
   *lnl = acc;
   if (GRAD)
 #pragma unroll
-    for (int i = 0; i < SHARPY_NPHYS; ++i) gph[i] = g[i];
+    for (int i = 0; i < SHARPY_NPHYS; ++i) gph[i] = (double)g[i];
 }
 
 // Diagonal Gaussian mixture (test targets): ln L and its gradient.

@@ -62,7 +62,7 @@ extern "C" int sharpy_smc_run(sharpy_ctx* c, const sharpy_smc_options* o, uint64
   if (!o || !lnz || o->n_particles < 1 || o->n_particles > ((int64_t)1 << 20) || !(o->alpha > 0.0 && o->alpha <= 1.0) ||
       o->n_mut < 0 || o->max_depth < 0 || o->max_depth > SHARPY_MAX_DEPTH || o->max_stages < 1 ||
       !(o->eps_scale > 0.0) || (o->metric != 0 && o->metric != 1) ||
-      (o->precision != SHARPY_FP64 && o->precision != SHARPY_MIXED))
+      (o->precision != SHARPY_FP64 && o->precision != SHARPY_MIXED && o->precision != SHARPY_MIXED_SPLIT))
     return SHARPY_EINVAL;
   const int64_t n = o->n_particles;
   const int D = c->model.n_dim;

@@ -64,20 +64,27 @@ static __device__ EssSums ess_sums(const double* lnl, int64_t n, double mx, doub
 }
 
 // Single-CTA stage kernel. Solves ESS(db) = alpha N for the tempering
-// increment (Eq. 6) by a safeguarded Newton iteration on
-// g(db) = 2 ln S1 - ln S2 - ln(alpha N) inside a shrinking bisection bracket
-// (ESS decreases with db), converged to adjacent doubles; then writes
-// W = e^{db (lnL - max)}, the integer prefix sums C of floor(W 2^32), the
-// ESS, dlnz, beta_next, the covariance, and updates ln Z.
+// increment (Eq. 6). ESS decreases with db and S2(db) = S1(2 db), so one FP32
+// pass over the geometric grid db_m = hi 2^-m (m = -1..kGrid-2) brackets the
+// root within a factor of two; a Newton iteration on g(db) = 2 ln S1 - ln S2 -
+// ln(alpha N) in FP64, safeguarded by that bracket, then closes it to adjacent
+// doubles. Writes W = e^{db (lnL - max)}, the integer prefix sums C of
+// floor(W 2^32), the ESS, dlnz, beta_next, the covariance, and updates ln Z.
+constexpr int kGrid = 54;
+constexpr int kGridChunk = 9;
+
 __global__ void __launch_bounds__(kSmcThreads)
 reweight_kernel(int64_t n, const double* __restrict__ lnl, const double* __restrict__ theta, int D,
                 const double* beta_prev_ptr, double beta_prev_val, double alpha, double* __restrict__ w_out,
                 unsigned long long* __restrict__ csum, double* beta_next, double* dlnz, double* ess_out,
                 double* cov, double* lnz_acc, double* beta_state, int* status) {
   __shared__ double red[32];
+  __shared__ float redf[kGridChunk][32];
+  __shared__ float s1grid[kGrid];
   __shared__ double sh_db;
   __shared__ unsigned long long carry[kSmcThreads];
   const double beta_prev = beta_prev_ptr ? *beta_prev_ptr : beta_prev_val;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   double mx = -INFINITY;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
     if (isfinite(lnl[i])) mx = fmax(mx, lnl[i]);
@@ -96,22 +103,59 @@ reweight_kernel(int64_t n, const double* __restrict__ lnl, const double* __restr
     if (ess_hi >= target) {
       if (threadIdx.x == 0) sh_db = hi;
     } else {
-      double lo = 0.0, x = 0.5 * hi;
+      // FP32 grid: s1grid[m] = S1(hi 2^(1-m)), so g(hi 2^-m) uses s1grid[m+1] and s1grid[m]
+      for (int c0 = 0; c0 < kGrid; c0 += kGridChunk) {
+        float acc[kGridChunk];
+#pragma unroll
+        for (int c = 0; c < kGridChunk; ++c) acc[c] = 0.0f;
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+          double l = lnl[i];
+          if (!isfinite(l)) continue;
+          const float x = (float)((l - mx) * hi * 1.4426950408889634);  // log2(e) * db0 * x
+#pragma unroll
+          for (int c = 0; c < kGridChunk; ++c) acc[c] += exp2f(ldexpf(x, 1 - (c0 + c)));
+        }
+#pragma unroll
+        for (int c = 0; c < kGridChunk; ++c) {
+          float v = warp_sum(acc[c]);
+          if (lane == 0) redf[c][warp] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < kGridChunk) {
+          float t = 0.0f;
+          for (int w = 0; w < nwarp; ++w) t += redf[threadIdx.x][w];
+          s1grid[c0 + threadIdx.x] = t;
+        }
+        __syncthreads();
+      }
+      // largest grid point with ESS >= target: bracket [hi 2^-m, hi 2^(1-m)]
+      int m = 1;
+      while (m < kGrid - 1 && 2.0f * logf(s1grid[m + 1]) - logf(s1grid[m]) < (float)lt) ++m;
+      double lo = (m < kGrid - 1) ? ldexp(hi, -m) : 0.0;
+      double up = ldexp(hi, 1 - m);
+      // the FP32 bracket may be one cell off near the crossing: widen until FP64 agrees
+      for (int k = 0; k < 4 && lo > 0.0; ++k) {
+        EssSums a = ess_sums(lnl, n, mx, lo, red);
+        if (2.0 * log(a.s1) - log(a.s2) - lt >= 0.0) break;
+        up = lo;
+        lo = (k == 3) ? 0.0 : 0.5 * lo;
+      }
+      double x = lo > 0.0 ? sqrt(lo * up) : 0.5 * up;
       for (int it = 0; it < 200; ++it) {
-        EssSums s = ess_sums(lnl, n, mx, x, red);
-        double g = 2.0 * log(s.s1) - log(s.s2) - lt;
+        EssSums sm = ess_sums(lnl, n, mx, x, red);
+        double g = 2.0 * log(sm.s1) - log(sm.s2) - lt;
         if (g >= 0.0)
           lo = x;
         else
-          hi = x;
+          up = x;
         // Newton step on g; g' = 2 (S1x/S1 - S2x/S2)
-        double gp = 2.0 * (s.s1x / s.s1 - s.s2x / s.s2);
+        double gp = 2.0 * (sm.s1x / sm.s1 - sm.s2x / sm.s2);
         double xn = x - g / gp;
-        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+        if (!(xn > lo && xn < up)) xn = 0.5 * (lo + up);
         // once Newton moves by an ulp or two, probe the neighbouring double so the
         // bracket closes to adjacent doubles
-        if (fabs(xn - x) <= 4.440892098500626e-16 * fabs(x)) xn = (g >= 0.0) ? nextafter(x, hi) : nextafter(x, lo);
-        if (!(xn > lo && xn < hi)) break;  // lo and hi are adjacent doubles
+        if (fabs(xn - x) <= 4.440892098500626e-16 * fabs(x)) xn = (g >= 0.0) ? nextafter(x, up) : nextafter(x, lo);
+        if (!(xn > lo && xn < up)) break;  // lo and up are adjacent doubles
         x = xn;
       }
       if (threadIdx.x == 0) sh_db = lo;

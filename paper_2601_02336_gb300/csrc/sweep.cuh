@@ -7,12 +7,17 @@
 // Z_a (and, for the gradient, Y_aj = sum z B_j).
 //
 //   SHARPY_FP64  : FP64 throughout; reduction Psi - rint(Psi); sincospi.
+//   SHARPY_MIXED_SPLIT : as SHARPY_MIXED, but the phase polynomial is built
+//                  from hi/lo FP32 splits of alpha_j, tau_a and B_j(f_k):
+//                  each product's integer turns are removed exactly (FMA error
+//                  term kept), the fraction stays in [-1/2, 1/2]; no FP64 in
+//                  the bin loop (worst-case phase error ~3e-7 turns).
 //   SHARPY_MIXED : FP64 phase accumulated on top of the offset 1.5 * 2^20
 //                  turns, whose low mantissa word is the fractional turn in
 //                  2^-32 units; FP32 sincos, carrier and moments. Per-lane
 //                  FP32 partial sums are flushed every kFlush iterations
-//                  through a fixed-order warp tree into FP64 accumulators
-//                  (blocked pairwise summation).
+//                  through a fixed-order warp tree into compensated FP32
+//                  outer accumulators (blocked pairwise summation).
 #pragma once
 #include "physics.cuh"
 
@@ -34,29 +39,45 @@ __device__ __forceinline__ int acc_to_mom(int i) {
   return mom_index(i / 2, 9, i & 1);
 }
 
-// Flush per-lane FP32 partials into the lane-distributed FP64 accumulators.
+// Flush per-lane FP32 partials into the lane-distributed outer accumulators:
+// each block sum (fixed-order warp tree) is added with an error-free two-sum,
+// so the outer sums carry ~48 bits without FP64 arithmetic.
 template <int NACC>
-__device__ __forceinline__ void flush(float* acc, double* outer, int lane) {
+__device__ __forceinline__ void flush(float* acc, float* hi, float* lo, int lane) {
 #pragma unroll
   for (int i = 0; i < NACC; ++i) {
     float v = warp_sum(acc[i]);
-    if ((i & 31) == lane) outer[i >> 5] += (double)v;
+    if ((i & 31) == lane) {
+      const int o = i >> 5;
+      const float s = hi[o] + v;
+      const float bp = s - hi[o];
+      lo[o] += (hi[o] - (s - bp)) + (v - bp);
+      hi[o] = s;
+    }
     acc[i] = 0.0f;
   }
 }
 
-template <bool GRAD, int NDET>
-__device__ void sweep_mixed(const DevEvent& ev, const SweepCoef& sc, double* mom) {
+// Magic constant for exact round-to-nearest of |x| < 2^22 in FP32.
+constexpr float kRound32 = 12582912.0f;  // 1.5 * 2^23
+
+// x - rint(x) for |x| < 2^22, exact (explicit roundings: no contraction).
+__device__ __forceinline__ float frac_turn(float x) {
+  return __fsub_rn(x, __fsub_rn(__fadd_rn(x, kRound32), kRound32));
+}
+
+template <bool GRAD, int NDET, bool SPLIT>
+__device__ void sweep_mixed(const DevEvent& ev, const SweepCoef& sc, float* mom) {
   constexpr int NACC = MomCount<NDET, GRAD>::value;
   constexpr int NOUT = (NACC + 31) / 32;
   const int lane = threadIdx.x & 31;
   const int64_t K = ev.n_bins;
   float acc[NACC];
-  double outer[NOUT];
+  float hi[NOUT], lo[NOUT];
 #pragma unroll
   for (int i = 0; i < NACC; ++i) acc[i] = 0.0f;
 #pragma unroll
-  for (int i = 0; i < NOUT; ++i) outer[i] = 0.0;
+  for (int i = 0; i < NOUT; ++i) hi[i] = lo[i] = 0.0f;
   double al[kNPn];
 #pragma unroll
   for (int j = 0; j < kNPn; ++j) al[j] = sc.alpha[j];
@@ -64,26 +85,67 @@ __device__ void sweep_mixed(const DevEvent& ev, const SweepCoef& sc, double* mom
 #pragma unroll
   for (int a = 0; a < NDET; ++a) tau[a] = sc.tau[a];
   const double s0 = sc.c0 + kTurnOffset;
+  float ah[kNPn], alo[kNPn], th[NDET], tl[NDET];
+  if (SPLIT) {
+#pragma unroll
+    for (int j = 0; j < kNPn; ++j) {
+      ah[j] = sc.ahi[j];
+      alo[j] = sc.alo[j];
+    }
+#pragma unroll
+    for (int a = 0; a < NDET; ++a) {
+      th[a] = sc.thi[a];
+      tl[a] = sc.tlo[a];
+    }
+  }
   const int kend = sc.kisco;
   int it = 0;
   // Warp-uniform trip count: lanes past k_ISCO idle but still join the flushes.
   for (int k0 = 0; k0 <= kend; k0 += 32) {
     const int k = k0 + lane;
     if (k <= kend) {
-    double S = s0;
-#pragma unroll
-    for (int j = 0; j < kNPn; ++j) S = fma(al[j], __ldg(ev.b64 + (int64_t)j * K + k), S);
-    const double f = __ldg(ev.b64 + (int64_t)8 * K + k);
     float bf[kNBasis];
-    if (GRAD) {
+    if (GRAD || SPLIT) {
 #pragma unroll
       for (int j = 0; j < kNBasis; ++j) bf[j] = __ldg(ev.b32 + (int64_t)j * K + k);
     }
+    // phase: FP64 accumulation on the turn offset, or split single precision
+    double S = s0, f = 0.0;
+    float F = 0.0f, Sm = 0.0f;
+    if (!SPLIT) {
+#pragma unroll
+      for (int j = 0; j < kNPn; ++j) S = fma(al[j], __ldg(ev.b64 + (int64_t)j * K + k), S);
+      f = __ldg(ev.b64 + (int64_t)8 * K + k);
+    } else {
+      // sum_j alpha_j B_j mod 1: p = ahi*bhi is exact up to e (FMA), its integer
+      // part is removed exactly, the fraction accumulates in F (kept in
+      // [-1/2, 1/2]), the error and cross terms in Sm.
+      F = sc.c0f;
+#pragma unroll
+      for (int j = 0; j < kNPn; ++j) {
+        const float bl = __ldg(ev.b32lo + (int64_t)j * K + k);
+        const float p = __fmul_rn(ah[j], bf[j]);
+        Sm += fmaf(ah[j], bf[j], -p);
+        Sm = fmaf(ah[j], bl, fmaf(alo[j], bf[j], Sm));
+        F = __fadd_rn(F, frac_turn(p));
+        if (j & 1) F = frac_turn(F);
+      }
+    }
 #pragma unroll
     for (int a = 0; a < NDET; ++a) {
-      const double P = fma(f, tau[a], S);
-      const int turn = __double2loint(P);  // fractional turn, 2^-32 units
-      const float ang = (float)turn * 1.46291807926715968e-9f;  // 2 pi / 2^32
+      float ang;
+      if (!SPLIT) {
+        const double P = fma(f, tau[a], S);
+        const int turn = __double2loint(P);  // fractional turn, 2^-32 units
+        ang = (float)turn * 1.46291807926715968e-9f;  // 2 pi / 2^32
+      } else {
+        const float fl = __ldg(ev.b32lo + (int64_t)8 * K + k);
+        const float p = __fmul_rn(th[a], bf[8]);
+        float Sa = Sm + fmaf(th[a], bf[8], -p);
+        Sa = fmaf(th[a], fl, fmaf(tl[a], bf[8], Sa));
+        const float Fa = frac_turn(__fadd_rn(F, frac_turn(p)));
+        ang = (Fa + Sa) * 6.28318530717958648f;
+      }
       float sn, cs;
       __sincosf(ang, &sn, &cs);
       const float2 E = __ldg(ev.e32 + (int64_t)a * K + k);
@@ -104,16 +166,16 @@ __device__ void sweep_mixed(const DevEvent& ev, const SweepCoef& sc, double* mom
     }
     }
     if (++it == kFlush) {
-      flush<NACC>(acc, outer, lane);
+      flush<NACC>(acc, hi, lo, lane);
       it = 0;
     }
   }
   // Every lane takes part in the final flush (warp-uniform).
-  flush<NACC>(acc, outer, lane);
+  flush<NACC>(acc, hi, lo, lane);
 #pragma unroll
   for (int i = 0; i < NOUT; ++i) {
     int idx = i * 32 + lane;
-    if (idx < NACC) mom[acc_to_mom<NDET, GRAD>(idx)] = outer[i];
+    if (idx < NACC) mom[acc_to_mom<NDET, GRAD>(idx)] = hi[i] + lo[i];
   }
 }
 
@@ -169,12 +231,22 @@ __device__ void sweep_fp64(const DevEvent& ev, const SweepCoef& sc, double* mom)
   }
 }
 
+// Moment storage type of each path.
+template <int PREC>
+struct MomType {
+  using type = float;
+};
+template <>
+struct MomType<SHARPY_FP64> {
+  using type = double;
+};
+
 template <int PREC, bool GRAD, int NDET>
-__device__ __forceinline__ void sweep(const DevEvent& ev, const SweepCoef& sc, double* mom) {
-  if (PREC == SHARPY_FP64)
+__device__ __forceinline__ void sweep(const DevEvent& ev, const SweepCoef& sc, typename MomType<PREC>::type* mom) {
+  if constexpr (PREC == SHARPY_FP64)
     sweep_fp64<GRAD, NDET>(ev, sc, mom);
   else
-    sweep_mixed<GRAD, NDET>(ev, sc, mom);
+    sweep_mixed<GRAD, NDET, PREC == SHARPY_MIXED_SPLIT>(ev, sc, mom);
 }
 
 }  // namespace sharpy

@@ -65,13 +65,14 @@ def test_loglike_grad_fp64(name):
     _check(w, ev, ctx, thetas, lambda r: 1e-7 + 1e-10 * np.abs(r), 1e-8, "fp64")
 
 
+@pytest.mark.parametrize("precision", ["mixed", "split"])
 @pytest.mark.parametrize("name", ["tiny", "bbh11", "bbh11_long"])
-def test_loglike_grad_mixed(name):
+def test_loglike_grad_mixed(name, precision):
     G.require_gpu()
     w = inputs.WORKLOADS[name]()
     ev, ctx, th_inj, _ = G.event_pair(w)
     thetas = _thetas(w, th_inj, 35, 29, 60)
-    _check(w, ev, ctx, thetas, lambda r: 1e-3 + 0 * r, 1e-4, "mixed")
+    _check(w, ev, ctx, thetas, lambda r: 1e-3 + 0 * r, 1e-4, precision)
 
 
 def test_loglike_long_signal_sampled():
@@ -81,6 +82,7 @@ def test_loglike_long_signal_sampled():
     ev, ctx, th_inj, _ = G.event_pair(w)
     thetas = _thetas(w, th_inj, 9, 7, 70)
     _check(w, ev, ctx, thetas, lambda r: 1e-2 + 0 * r, 1e-4, "mixed")
+    _check(w, ev, ctx, thetas, lambda r: 1e-2 + 0 * r, 1e-4, "split")
     _check(w, ev, ctx, thetas[:6], lambda r: 1e-6 + 1e-10 * np.abs(r), 1e-8, "fp64")
 
 
@@ -134,7 +136,7 @@ def test_edge_cases():
     # single particle, and a mass above the band: f_ISCO < f_min, no bins -> lnL = -<d|d>/2
     th = th_inj.copy()
     th[0] = 400.0
-    for prec in ("fp64", "mixed"):
+    for prec in ("fp64", "mixed", "split"):
         l, g = ctx.loglike_grad(G.to_dev(th[None, :]), prec)
         ref = oracle.loglike(model, ev, th[None, :], grad=False)[0]
         assert float(l[0]) == pytest.approx(ref, rel=1e-12)

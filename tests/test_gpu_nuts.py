@@ -81,8 +81,9 @@ def test_nuts_taylorf2_fp64_matches_oracle():
         assert st["active_bins"].sum() > 0
 
 
-def test_nuts_taylorf2_11d_mixed_vs_fp64():
-    """The mixed sweep changes H by ~1e-4 at most, so most trajectories stay identical to the FP64 ones."""
+@pytest.mark.parametrize("precision", ["mixed", "split"])
+def test_nuts_taylorf2_11d_mixed_vs_fp64(precision):
+    """The mixed sweeps change H by ~1e-4 at most, so most trajectories stay identical to the FP64 ones."""
     G.require_gpu()
     w = inputs.bbh11()
     ev, ctx, th_inj, _ = G.event_pair(w)
@@ -91,16 +92,16 @@ def test_nuts_taylorf2_11d_mixed_vs_fp64():
     t0 = G.to_dev(th)
     l0, g0 = ctx.loglike_grad(t0, "fp64")
     out = {}
-    for prec in ("fp64", "mixed"):
+    for prec in ("fp64", precision):
         t, l, g = t0.clone(), l0.clone(), g0.clone()
         st = ctx.nuts_mutate(0.7, t, l, g, None, 1e-5, 6, 2, key=5, ctr=1, precision=prec)
         out[prec] = (t.cpu().numpy(), l.cpu().numpy(), api.Context.stats_to_numpy(st))
-    dev = np.max(np.abs(out["fp64"][0] - out["mixed"][0]) / G.width(w)[None, :], axis=1)
+    dev = np.max(np.abs(out["fp64"][0] - out[precision][0]) / G.width(w)[None, :], axis=1)
     assert np.mean(dev < 1e-6) >= 0.8
-    assert np.all(np.isfinite(out["mixed"][0]))
-    # self-consistency of the mixed outputs
-    l2, _ = ctx.loglike_grad(G.to_dev(out["mixed"][0]), "mixed")
-    assert np.allclose(l2.cpu().numpy(), out["mixed"][1], rtol=0, atol=1e-6)
+    assert np.all(np.isfinite(out[precision][0]))
+    # self-consistency of the outputs
+    l2, _ = ctx.loglike_grad(G.to_dev(out[precision][0]), precision)
+    assert np.allclose(l2.cpu().numpy(), out[precision][1], rtol=0, atol=1e-6)
     assert ctx.status() == 0
 
 

@@ -72,7 +72,8 @@ def test_run_fp64_vs_oracle():
     assert abs(np.mean(got) - np.mean(ref)) <= 2.0 * math.sqrt(_se(got) ** 2 + _se(ref) ** 2), (got, ref)
 
 
-def test_run_mixed_lnz_within_two_se():
+@pytest.mark.parametrize("precision", ["mixed", "split"])
+def test_run_mixed_lnz_within_two_se(precision):
     G.require_gpu()
     w = inputs.tiny()
     ev, ctx, th_inj, _ = G.event_pair(w)
@@ -81,6 +82,6 @@ def test_run_mixed_lnz_within_two_se():
     ref = [oracle.smc_run(model, ev, w.n_particles, w.alpha, w.n_mut, w.max_depth, w.metric, w.eps_scale,
                           key=60 + s)[0] for s in range(R)]
     got = [ctx.smc_run(w.n_particles, w.alpha, w.n_mut, w.max_depth, w.metric, w.eps_scale, key=80 + s,
-                       precision="mixed")[0] for s in range(R)]
+                       precision=precision)[0] for s in range(R)]
     assert abs(np.mean(got) - np.mean(ref)) <= 2.0 * math.sqrt(_se(got) ** 2 + _se(ref) ** 2), (got, ref)
     assert ctx.status() == 0
