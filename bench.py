@@ -172,12 +172,10 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from paper_2601_02336_gb300 import api, inputs
+    from paper_2601_02336_gb300 import api, inputs, multirank
     from paper_2601_02336_gb300._lib import lib
 
-    world = _env_int("WORLD_SIZE", 1)
-    rank = _env_int("RANK", 0)
-    local = _env_int("LOCAL_RANK", 0)
+    rank, world, local = multirank.env_rank()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
@@ -188,21 +186,13 @@ def main():
         torch.cuda.synchronize()
 
     def allmax(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t[0])
+        return multirank.reduce_scalar(x, "max", world, device="cuda")
 
     def allsum(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t[0])
+        return multirank.reduce_scalar(x, "sum", world, device="cuda")
 
     w = inputs.bbh11()
-    ctx, th_inj, data = api.make_event(w, seed=rank, device=local)
+    ctx, th_inj, data = api.make_event(w, seed=multirank.event_seed(rank), device=local)
     run_args = (w.n_particles, w.alpha, w.n_mut, w.max_depth, w.metric, w.eps_scale)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
@@ -210,7 +200,7 @@ def main():
         return ctx.smc_run(*run_args, key=key, precision=precision, timing=timing)
 
     for i in range(args.warmup):
-        one_run(10_000 + 1000 * rank + i, args.precision)
+        one_run(multirank.run_key(10_000, rank, i), args.precision)
     stream = torch.cuda.current_stream()
     clocks = ClockSampler(local)
     clocks.start()
@@ -218,6 +208,7 @@ def main():
     evals = 0
     bins = 0.0
     nuts_ms = 0.0
+    rew_ms = 0.0
     launches = 0
     step_ms = []
     lnzs = []
@@ -226,13 +217,14 @@ def main():
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        lnz, th, ll, rec = one_run(20_000 + 1000 * rank + k, args.precision)
+        lnz, th, ll, rec = one_run(multirank.run_key(20_000, rank, k), args.precision)
         e1.record(stream)
         torch.cuda.synchronize()
         step_ms.append(e0.elapsed_time(e1))
         evals += sum(r["n_leapfrog"] for r in rec)
         bins += sum(r["active_bins"] for r in rec)
         nuts_ms += sum(r["nuts_ms"] for r in rec)
+        rew_ms += sum(r["reweight_ms"] for r in rec)
         launches += 2 + 5 * len(rec)
         lnzs.append(lnz)
         n_stages.append(len(rec))
@@ -260,6 +252,7 @@ def main():
                 "fp32_achieved": fp32_ach, "fp32_peak": fp32_peak,
                 "fp32_frac": fp32_ach / fp32_peak if fp32_peak else None, "fp64_peak": fp64_peak,
                 "nuts_share_of_step": nuts_ms / t_rank,
+                "reweight_share_of_step": rew_ms / t_rank,
                 "active_bin_det_per_eval": bins / max(evals, 1)}
 
     # the other precision for the mixed-vs-FP64 comparison and |d lnZ| <= 2 sigma
@@ -270,7 +263,7 @@ def main():
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            lnz, th, ll, rec = one_run(30_000 + 1000 * rank + k, "fp64")
+            lnz, th, ll, rec = one_run(multirank.run_key(30_000, rank, k), "fp64")
             e1.record(stream)
             torch.cuda.synchronize()
             t_o += e0.elapsed_time(e1)
@@ -300,7 +293,7 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             ctx.set_data(h_data.numpy(), h_psd.numpy(), w.f_min, w.df, dets)
-            lnz, th, ll, rec = one_run(40_000 + 1000 * rank + k, args.precision, timing=False)
+            lnz, th, ll, rec = one_run(multirank.run_key(40_000, rank, k), args.precision, timing=False)
             th_h = th.cpu()
             ll_h = ll.cpu()
             torch.cuda.synchronize()

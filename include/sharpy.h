@@ -129,6 +129,7 @@ typedef struct {
   int pad;
   double active_bins;  /* sum over the stage's gradient evaluations of (bins below f_ISCO) x detectors */
   double nuts_ms;      /* duration of the stage's NUTS launch (opt->timing = 1), else 0 */
+  double reweight_ms;  /* duration of the stage's reweight/resample/gather (opt->timing = 1), else 0 */
 } sharpy_stage;
 
 /* Context. Owns the staged data tables, scratch, the evidence accumulator and

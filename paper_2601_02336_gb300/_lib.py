@@ -49,7 +49,8 @@ class Stage(C.Structure):
     _fields_ = [("beta", C.c_double), ("dbeta", C.c_double), ("ess", C.c_double),
                 ("dlnz", C.c_double), ("eps", C.c_double), ("accept_mean", C.c_double),
                 ("depth_mean", C.c_double), ("n_leapfrog", C.c_int64), ("n_divergent", C.c_int),
-                ("pad", C.c_int), ("active_bins", C.c_double), ("nuts_ms", C.c_double)]
+                ("pad", C.c_int), ("active_bins", C.c_double), ("nuts_ms", C.c_double),
+                ("reweight_ms", C.c_double)]
 
 
 _VP = C.c_void_p

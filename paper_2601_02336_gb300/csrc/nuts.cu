@@ -55,12 +55,8 @@ int enqueue_nuts(sharpy_ctx* c, int64_t n, const double* beta_ptr, double beta, 
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // widest slot count that still gives about one CTA per SM
-  int slots = 8;
-  if (n >= (int64_t)32 * sms * 4 / 5)
-    slots = 32;
-  else if (n >= (int64_t)16 * sms * 4 / 5)
-    slots = 16;
+  // widest slot count that still gives about two CTAs per SM
+  const int slots = n >= (int64_t)16 * 2 * sms * 3 / 4 ? 16 : 8;
   const int nd = c->model.model == SHARPY_MODEL_TAYLORF2 ? c->ev.n_det : 1;
   return launch_nuts(precision, nd, slots, A, s);
 }

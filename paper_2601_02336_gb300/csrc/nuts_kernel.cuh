@@ -2,24 +2,34 @@
 // variant with biased progressive sampling at the top level and the
 // generalised U-turn criterion on every completed sub-tree).
 //
-// One CTA of kNutsWarps warps owns SLOTS (8, 16 or 32) particles for the whole
-// call; SLOTS is chosen from N so that the CTAs about fill the GPU in one wave
-// while warp 0's per-particle phase runs on as many lanes as possible (an FP64
-// warp instruction costs the same pipe time whatever its active-lane count).
-// Lane s of warp 0 runs the NUTS state machine of slot s: the trajectory is grown one
-// leapfrog at a time (iteratively, no recursion), and every leapfrog needs one
-// likelihood+gradient evaluation. Each "tick" of the CTA: warp 0 computes the
-// prologue of every pending evaluation (lane-parallel), each warp sweeps the
-// bins of one pending particle, warp 0 runs the epilogues and advances the
-// state machines to their next evaluation. Particles with shallow trees finish
-// early and leave their lane idle; the tree state of every slot lives in shared
-// memory ([field][dim][slot], conflict-free across lanes).
+// One CTA of kNutsWarps warps owns SLOTS (8 or 16) particles for the whole
+// call; SLOTS is chosen from N so that about two CTAs share each SM (their
+// serial per-particle phases then overlap with each other's sweeps) while warp
+// 0's per-particle phase runs on as many lanes as possible (an FP64 warp
+// instruction costs the same pipe time whatever its active-lane count).
+// Lane s of warp 0 runs the NUTS state machine of slot s: the trajectory is
+// grown one leapfrog at a time (iteratively, no recursion), and every leapfrog
+// needs one likelihood+gradient evaluation. Each "tick" of the CTA: warp 0
+// computes the prologue of every pending evaluation (lane-parallel), each warp
+// sweeps the bins of one pending particle, warp 0 runs the epilogues and
+// advances the state machines to their next evaluation. Particles with shallow
+// trees finish early and leave their lane idle; the tree state of every slot
+// lives in shared memory ([field][dim][slot], conflict-free across lanes).
+//
+// Precision of the tree state (template VT): positions theta and the potential
+// energy are FP64 on every path. The FP64 path keeps momenta, velocities,
+// momentum sums, gradients, log-weights and random draws in FP64 too. The
+// mixed paths keep those in FP32: a dependent FP64 operation costs ~64 cycles
+// on this GPU (FP32: ~4) and an FP64 exp ~1200, and this state machine is a
+// serial chain per particle; FP32 resolves the momenta and weights far below
+// the mixed likelihood's own error.
 //
 // Leaf order and random draws (Philox4x32-10, counter = (particle, step,
 // purpose, index)): per transition the momentum (purpose 2, one normal pair
 // per index), per doubling j the direction (purpose 3, index j) and the
 // top-level acceptance (purpose 5, index j), per leaf the in-subtree
-// progressive acceptance (purpose 4, running leaf index).
+// progressive acceptance (purpose 4, running leaf index). FP64 draws use 53
+// bits of the first two words; FP32 draws use the top 24 bits of the first.
 #pragma once
 #include <cmath>
 
@@ -28,20 +38,21 @@
 
 namespace sharpy {
 
-constexpr int kNutsWarps = 8;
+constexpr int kNutsWarps = 4;  // warps per CTA; two CTAs share an SM so their serial phases interleave
 constexpr int kMaxDepth = SHARPY_MAX_DEPTH;
 constexpr double kDivergence = 1000.0;
 
-// Shared-memory vector fields of the tree state.
+// Position fields (FP64).
+enum { P_L, P_R, P_P, P_S, P_N, P_COUNT };  // left end, right end, proposal, sub-tree proposal, pending leaf
+// Momentum-like fields (type VT).
 enum {
-  F_LTH, F_LR, F_LGU, F_LV,  // left end: theta, momentum, grad U, velocity Minv r
-  F_RTH, F_RR, F_RGU, F_RV,  // right end
-  F_PTH, F_PGL,              // proposal (also the current point between transitions)
-  F_STH, F_SGL,              // sub-tree proposal
-  F_RHO, F_RHOS,             // momentum sums: whole tree, current sub-tree
-  F_NTH, F_NR,               // pending leaf: position, half-step momentum
-  F_RS0,                     // rho_start[1..kMaxDepth]
-  F_RF0 = F_RS0 + kMaxDepth, // velocity of the first leaf of each open block [1..kMaxDepth]
+  F_LR, F_LGU, F_LV,          // left end: momentum, grad U, velocity Minv r
+  F_RR, F_RGU, F_RV,          // right end
+  F_PGL, F_SGL,               // grad ln L of the proposal / sub-tree proposal
+  F_RHO, F_RHOS,              // momentum sums: whole tree, current sub-tree
+  F_NR,                       // pending leaf: half-step momentum
+  F_RS0,                      // rho_start[1..kMaxDepth]
+  F_RF0 = F_RS0 + kMaxDepth,  // velocity of the first leaf of each open block [1..kMaxDepth]
   F_COUNT = F_RF0 + kMaxDepth
 };
 
@@ -67,11 +78,12 @@ struct NutsArgs {
 
 enum { METRIC_IDENTITY = 0, METRIC_DIAGONAL = 1, METRIC_DENSE = 2 };
 
-template <int SLOTS>
+template <int SLOTS, class VT>
 struct NutsShared {
-  double vec[F_COUNT][kMaxDim][SLOTS];
-  double minv[kMaxDim][kMaxDim];
-  double chol[kMaxDim][kMaxDim];
+  double pos[P_COUNT][kMaxDim][SLOTS];
+  VT vec[F_COUNT][kMaxDim][SLOTS];
+  VT minv[kMaxDim][kMaxDim];
+  VT chol[kMaxDim][kMaxDim];
   double eps, beta;
   double lp_const;  // sum of the prior's constant log terms
   int metric_kind;
@@ -79,14 +91,39 @@ struct NutsShared {
   int pending[SLOTS];
 };
 
-__device__ __forceinline__ double logaddexp(double a, double b) {
+// Elementary functions in the state machine's precision.
+__device__ __forceinline__ double vexp(double x) { return exp(x); }
+__device__ __forceinline__ float vexp(float x) { return expf(x); }
+__device__ __forceinline__ double vlog(double x) { return log(x); }
+__device__ __forceinline__ float vlog(float x) { return logf(x); }
+__device__ __forceinline__ double vsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float vsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ void vsincospi(double x, double* s, double* c) { sincospi(x, s, c); }
+__device__ __forceinline__ void vsincospi(float x, float* s, float* c) { sincospif(x, s, c); }
+
+template <class VT>
+__device__ __forceinline__ VT logaddexp(VT a, VT b) {
   if (a == -INFINITY) return b;
   if (b == -INFINITY) return a;
-  double mx = fmax(a, b);
-  return mx + log(exp(a - mx) + exp(b - mx));
+  VT mx = a > b ? a : b;
+  return mx + vlog(vexp(a - mx) + vexp(b - mx));
+}
+
+// Two uniforms in (0, 1) from one Philox block, in the state machine's precision.
+__device__ __forceinline__ void draw2(uint64_t key, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, double* u0,
+                                      double* u1) {
+  uniform2(key, c0, c1, c2, c3, u0, u1);
+}
+__device__ __forceinline__ void draw2(uint64_t key, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, float* u0,
+                                      float* u1) {
+  uint32_t x[4];
+  philox4x32_10(c0, c1, c2, c3, (uint32_t)key, (uint32_t)(key >> 32), x);
+  *u0 = ((float)(x[0] >> 8) + 0.5f) * 5.9604644775390625e-8f;  // 2^-24
+  *u1 = ((float)(x[2] >> 8) + 0.5f) * 5.9604644775390625e-8f;
 }
 
 // Per-slot state machine (registers of lane s of warp 0).
+template <class VT>
 struct Slot {
   int64_t pid;
   int t;           // transition index
@@ -94,10 +131,11 @@ struct Slot {
   long n;          // leaf index within the current sub-tree
   int dir;
   uint32_t leaf_ctr;
-  double h0, logw, logw_sub, lnl_p, lnl_s, acc;
+  double h0;       // Hamiltonian at the start of the transition
+  double lnl_p, lnl_s, lnl_new;
+  VT logw, logw_sub, acc;
   int n_leaf, divergent;
   int done;
-  double u_cur, lnl_new;
   // stats
   double st_acc, st_bins;
   int st_depth, st_leap, st_div;
@@ -105,59 +143,61 @@ struct Slot {
 
 template <int PREC, int NDET, int SLOTS>
 struct Nuts {
-  using DT = typename std::conditional<PREC == SHARPY_FP64, double, float>::type;
+  using VT = typename std::conditional<PREC == SHARPY_FP64, double, float>::type;
   const NutsArgs& A;
-  NutsShared<SLOTS>& S;
+  NutsShared<SLOTS, VT>& S;
   int s;  // slot
   int D;
-  __device__ Nuts(const NutsArgs& a, NutsShared<SLOTS>& sh, int slot) : A(a), S(sh), s(slot), D(a.m.n_dim) {}
-  __device__ double& V(int f, int d) { return S.vec[f][d][s]; }
+  __device__ Nuts(const NutsArgs& a, NutsShared<SLOTS, VT>& sh, int slot) : A(a), S(sh), s(slot), D(a.m.n_dim) {}
+  __device__ VT& V(int f, int d) { return S.vec[f][d][s]; }
+  __device__ double& X(int f, int d) { return S.pos[f][d][s]; }
 
   // v = Minv r for the momentum stored in field f
-  __device__ void velocity(int f, double* v) {
+  __device__ void velocity(int f, VT* v) {
     if (S.metric_kind == METRIC_IDENTITY) {
       for (int i = 0; i < D; ++i) v[i] = V(f, i);
     } else if (S.metric_kind == METRIC_DIAGONAL) {
       for (int i = 0; i < D; ++i) v[i] = S.minv[i][i] * V(f, i);
     } else {
       for (int i = 0; i < D; ++i) {
-        double acc = 0.0;
+        VT acc = VT(0);
         for (int j = 0; j < D; ++j) acc += S.minv[i][j] * V(f, j);
         v[i] = acc;
       }
     }
   }
-  __device__ double dot(const double* a, int f) {
-    double k = 0.0;
+  __device__ VT dot(const VT* a, int f) {
+    VT k = VT(0);
     for (int i = 0; i < D; ++i) k += a[i] * V(f, i);
     return k;
   }
-  __device__ double dotv(const double* a, const double* b) {
-    double k = 0.0;
+  __device__ VT dotv(const VT* a, const VT* b) {
+    VT k = VT(0);
     for (int i = 0; i < D; ++i) k += a[i] * b[i];
     return k;
   }
-  // ln pi and grad ln pi with the constant terms precomputed
-  __device__ double prior(const double* x, double* g) {
+  // ln pi (FP64 total) and grad ln pi with the constant terms precomputed
+  __device__ double prior(const double* x, VT* g) {
     const DevModel& m = A.m;
     double lp = S.lp_const;
     bool inside = true;
     for (int i = 0; i < D; ++i) {
-      g[i] = 0.0;
+      g[i] = VT(0);
       if (!(x[i] >= m.lo[i] && x[i] <= m.hi[i])) inside = false;
       if (m.prior[i] == SHARPY_PRIOR_POWER2) {
-        lp += 2.0 * log(x[i]);
-        g[i] = 2.0 / x[i];
+        const VT xi = (VT)x[i];
+        lp += (double)(VT(2) * vlog(xi));
+        g[i] = VT(2) / xi;
       }
     }
     return inside ? lp : -INFINITY;
   }
 
-  // Boundary maps on the pending leaf (F_NTH, F_NR). False if not finite.
+  // Boundary maps on the pending leaf (P_N, F_NR). False if not finite.
   __device__ bool boundary() {
     const DevModel& m = A.m;
     for (int i = 0; i < D; ++i) {
-      double x = V(F_NTH, i);
+      double x = X(P_N, i);
       if (!isfinite(x)) return false;
       double lo = m.lo[i], hi = m.hi[i];
       if (m.boundary[i] == SHARPY_BOUND_PERIODIC) {
@@ -170,7 +210,7 @@ struct Nuts {
         else if (t < 0.0)
           t = t >= -w ? t : fmod(t, w);
         if (t < 0.0) t += w;
-        V(F_NTH, i) = lo + t;
+        X(P_N, i) = lo + t;
       } else {
         int flips = 0;
         while ((x < lo || x > hi) && flips < 100) {
@@ -178,11 +218,11 @@ struct Nuts {
           ++flips;
         }
         if (x < lo || x > hi) return false;
-        V(F_NTH, i) = x;
+        X(P_N, i) = x;
         if (flips & 1) {
-          double v[kMaxDim];
+          VT v[kMaxDim];
           velocity(F_NR, v);
-          V(F_NR, i) = V(F_NR, i) - 2.0 * v[i] / S.minv[i][i];
+          V(F_NR, i) = V(F_NR, i) - VT(2) * v[i] / S.minv[i][i];
         }
       }
     }
@@ -191,70 +231,73 @@ struct Nuts {
 
   // First half of a leapfrog from the end of the tree in direction dir.
   __device__ bool begin_leapfrog(int dir) {
-    const int fth = dir > 0 ? F_RTH : F_LTH, fr = dir > 0 ? F_RR : F_LR, fgu = dir > 0 ? F_RGU : F_LGU;
+    const int pth = dir > 0 ? P_R : P_L, fr = dir > 0 ? F_RR : F_LR, fgu = dir > 0 ? F_RGU : F_LGU;
     const double h = dir * S.eps;
-    for (int i = 0; i < D; ++i) V(F_NR, i) = V(fr, i) - 0.5 * h * V(fgu, i);
-    double v[kMaxDim];
+    const VT hv = (VT)h;
+    for (int i = 0; i < D; ++i) V(F_NR, i) = V(fr, i) - VT(0.5) * hv * V(fgu, i);
+    VT v[kMaxDim];
     velocity(F_NR, v);
-    for (int i = 0; i < D; ++i) V(F_NTH, i) = V(fth, i) + h * v[i];
+    for (int i = 0; i < D; ++i) X(P_N, i) = X(pth, i) + h * (double)v[i];
     return boundary();
   }
 
-  __device__ void draw_direction(Slot& sl) {
-    double u0, u1;
-    uniform2(A.key, (uint32_t)sl.pid, A.ctr + (uint32_t)sl.t, RNG_DIRECTION, (uint32_t)sl.depth, &u0, &u1);
-    sl.dir = u0 < 0.5 ? -1 : 1;
+  __device__ void draw_direction(Slot<VT>& sl) {
+    VT u0, u1;
+    draw2(A.key, (uint32_t)sl.pid, A.ctr + (uint32_t)sl.t, RNG_DIRECTION, (uint32_t)sl.depth, &u0, &u1);
+    sl.dir = u0 < VT(0.5) ? -1 : 1;
     sl.n = 0;
     sl.logw_sub = -INFINITY;
-    for (int i = 0; i < D; ++i) V(F_RHOS, i) = 0.0;
+    for (int i = 0; i < D; ++i) V(F_RHOS, i) = VT(0);
   }
 
-  // Start transition sl.t from the current point (F_PTH, F_PGL, lnl_p).
-  __device__ void start_transition(Slot& sl) {
+  // Start transition sl.t from the current point (P_P, F_PGL, lnl_p).
+  __device__ void start_transition(Slot<VT>& sl) {
     const uint32_t step = A.ctr + (uint32_t)sl.t;
-    double z[kMaxDim + 1];
+    VT z[kMaxDim + 1];
     for (int p = 0; 2 * p < D; ++p) {
-      double u0, u1;
-      uniform2(A.key, (uint32_t)sl.pid, step, RNG_MOMENTUM, (uint32_t)p, &u0, &u1);
-      double r = sqrt(-2.0 * log(u0));
-      double sn, cs;
-      sincospi(2.0 * u1, &sn, &cs);
+      VT u0, u1;
+      draw2(A.key, (uint32_t)sl.pid, step, RNG_MOMENTUM, (uint32_t)p, &u0, &u1);
+      VT r = vsqrt(VT(-2) * vlog(u0));
+      VT sn, cs;
+      vsincospi(VT(2) * u1, &sn, &cs);
       z[2 * p] = r * cs;
       z[2 * p + 1] = r * sn;
     }
     // r ~ N(0, M), M = Minv^{-1} = (L L^T)^{-1}: solve L^T r = z
     for (int i = D - 1; i >= 0; --i) {
-      double acc = z[i];
+      VT acc = z[i];
       for (int j = i + 1; j < D; ++j) acc -= S.chol[j][i] * V(F_LR, j);
       V(F_LR, i) = acc / S.chol[i][i];
     }
     // U and grad U at the current point
-    double x[kMaxDim], glp[kMaxDim], v0[kMaxDim];
-    for (int i = 0; i < D; ++i) x[i] = V(F_PTH, i);
-    double lp = prior(x, glp);
-    sl.u_cur = -S.beta * sl.lnl_p - lp;
+    double x[kMaxDim];
+    VT glp[kMaxDim], v0[kMaxDim];
+    for (int i = 0; i < D; ++i) x[i] = X(P_P, i);
+    const double lp = prior(x, glp);
+    const double u_cur = -S.beta * sl.lnl_p - lp;
+    const VT bv = (VT)S.beta;
     velocity(F_LR, v0);
     for (int i = 0; i < D; ++i) {
-      V(F_LTH, i) = x[i];
-      V(F_LGU, i) = -S.beta * V(F_PGL, i) - glp[i];
+      X(P_L, i) = x[i];
+      X(P_R, i) = x[i];
+      V(F_LGU, i) = -bv * V(F_PGL, i) - glp[i];
       V(F_LV, i) = v0[i];
-      V(F_RTH, i) = x[i];
       V(F_RR, i) = V(F_LR, i);
       V(F_RGU, i) = V(F_LGU, i);
       V(F_RV, i) = v0[i];
       V(F_RHO, i) = V(F_LR, i);
     }
-    sl.h0 = sl.u_cur + 0.5 * dot(v0, F_LR);
-    sl.logw = 0.0;
+    sl.h0 = u_cur + (double)(VT(0.5) * dot(v0, F_LR));
+    sl.logw = VT(0);
     sl.depth = 0;
     sl.leaf_ctr = 0;
-    sl.acc = 0.0;
+    sl.acc = VT(0);
     sl.n_leaf = 0;
     sl.divergent = 0;
   }
 
-  __device__ void end_transition(Slot& sl) {
-    sl.st_acc += sl.n_leaf > 0 ? sl.acc / sl.n_leaf : 0.0;
+  __device__ void end_transition(Slot<VT>& sl) {
+    sl.st_acc += sl.n_leaf > 0 ? (double)(sl.acc / (VT)sl.n_leaf) : 0.0;
     sl.st_depth += sl.depth;
     sl.st_leap += sl.n_leaf;
     sl.st_div += sl.divergent;
@@ -262,23 +305,24 @@ struct Nuts {
   }
 
   // Advance until the next evaluation is pending (true) or the slot is done.
-  // `have_leaf` : a leaf evaluation just finished (F_NTH/F_NR hold the leaf with
-  // full-step momentum, gl in F_SGL? no: passed in), process it first.
-  __device__ bool advance(Slot& sl, bool have_leaf, const double* gl_new, double lp_new, const double* glp_new) {
+  // have_leaf: a leaf evaluation just finished (P_N, F_NR hold its position and
+  // half-step momentum; lnl_new, gl_new, lp_new, glp_new its values).
+  __device__ bool advance(Slot<VT>& sl, bool have_leaf, const VT* gl_new, double lp_new, const VT* glp_new) {
     if (have_leaf) {
       // complete the leapfrog
-      const double h = sl.dir * S.eps;
-      double gu[kMaxDim];
+      const VT h = (VT)(sl.dir * S.eps);
+      const VT bv = (VT)S.beta;
+      VT gu[kMaxDim];
       for (int i = 0; i < D; ++i) {
-        gu[i] = -S.beta * gl_new[i] - glp_new[i];
-        V(F_NR, i) = V(F_NR, i) - 0.5 * h * gu[i];
+        gu[i] = -bv * gl_new[i] - glp_new[i];
+        V(F_NR, i) = V(F_NR, i) - VT(0.5) * h * gu[i];
       }
-      double u_new = -S.beta * sl.lnl_new - lp_new;
-      double vn[kMaxDim];
+      const double u_new = -S.beta * sl.lnl_new - lp_new;
+      VT vn[kMaxDim];
       velocity(F_NR, vn);
-      double dH = u_new + 0.5 * dot(vn, F_NR) - sl.h0;
+      const double dH = u_new + (double)(VT(0.5) * dot(vn, F_NR)) - sl.h0;
       sl.n_leaf += 1;
-      sl.acc += (dH == dH) ? fmin(1.0, exp(-dH)) : 0.0;
+      sl.acc += (dH == dH) ? (dH <= 0.0 ? VT(1) : vexp((VT)(-dH))) : VT(0);
       if (!(dH <= kDivergence)) {
         sl.divergent = 1;
         end_transition(sl);
@@ -286,21 +330,21 @@ struct Nuts {
       }
       {
         // the leaf becomes the end of the tree in direction dir
-        const int fth = sl.dir > 0 ? F_RTH : F_LTH, fr = sl.dir > 0 ? F_RR : F_LR, fgu = sl.dir > 0 ? F_RGU : F_LGU;
+        const int pth = sl.dir > 0 ? P_R : P_L, fr = sl.dir > 0 ? F_RR : F_LR, fgu = sl.dir > 0 ? F_RGU : F_LGU;
         const int fv = sl.dir > 0 ? F_RV : F_LV;
         for (int i = 0; i < D; ++i) {
-          V(fth, i) = V(F_NTH, i);
+          X(pth, i) = X(P_N, i);
           V(fr, i) = V(F_NR, i);
           V(fgu, i) = gu[i];
           V(fv, i) = vn[i];
         }
-        double lw = -dH;
-        double lw_new = logaddexp(sl.logw_sub, lw);
-        double u0, u1;
-        uniform2(A.key, (uint32_t)sl.pid, A.ctr + (uint32_t)sl.t, RNG_LEAF, sl.leaf_ctr++, &u0, &u1);
-        if (u0 < exp(lw - lw_new)) {
+        const VT lw = (VT)(-dH);
+        const VT lw_new = logaddexp(sl.logw_sub, lw);
+        VT u0, u1;
+        draw2(A.key, (uint32_t)sl.pid, A.ctr + (uint32_t)sl.t, RNG_LEAF, sl.leaf_ctr++, &u0, &u1);
+        if (u0 < vexp(lw - lw_new)) {
           for (int i = 0; i < D; ++i) {
-            V(F_STH, i) = V(F_NTH, i);
+            X(P_S, i) = X(P_N, i);
             V(F_SGL, i) = gl_new[i];
           }
           sl.lnl_s = sl.lnl_new;
@@ -316,9 +360,9 @@ struct Nuts {
         bool ok = true;
         for (int lvl = 1; lvl <= sl.depth && ok; ++lvl)
           if (((sl.n + 1) & ((1L << lvl) - 1)) == 0) {
-            double rb[kMaxDim];
+            VT rb[kMaxDim];
             for (int i = 0; i < D; ++i) rb[i] = V(F_RHOS, i) - V(F_RS0 + lvl - 1, i);
-            if (!(dot(rb, F_RF0 + lvl - 1) > 0.0 && dotv(rb, vn) > 0.0)) ok = false;
+            if (!(dot(rb, F_RF0 + lvl - 1) > VT(0) && dotv(rb, vn) > VT(0))) ok = false;
           }
         if (!ok) {
           end_transition(sl);
@@ -333,22 +377,22 @@ struct Nuts {
           goto next_transition;
         }
         // sub-tree complete: biased progressive sampling at the top level
-        uniform2(A.key, (uint32_t)sl.pid, A.ctr + (uint32_t)sl.t, RNG_TOP, (uint32_t)sl.depth, &u0, &u1);
-        if (u0 < exp(sl.logw_sub - sl.logw)) {
+        draw2(A.key, (uint32_t)sl.pid, A.ctr + (uint32_t)sl.t, RNG_TOP, (uint32_t)sl.depth, &u0, &u1);
+        if (u0 < vexp(sl.logw_sub - sl.logw)) {
           for (int i = 0; i < D; ++i) {
-            V(F_PTH, i) = V(F_STH, i);
+            X(P_P, i) = X(P_S, i);
             V(F_PGL, i) = V(F_SGL, i);
           }
           sl.lnl_p = sl.lnl_s;
         }
         sl.logw = logaddexp(sl.logw, sl.logw_sub);
-        double rho[kMaxDim];
+        VT rho[kMaxDim];
         for (int i = 0; i < D; ++i) {
           V(F_RHO, i) += V(F_RHOS, i);
           rho[i] = V(F_RHO, i);
         }
         sl.depth += 1;
-        if (!(dot(rho, F_LV) > 0.0 && dot(rho, F_RV) > 0.0) || sl.depth >= A.max_depth) {
+        if (!(dot(rho, F_LV) > VT(0) && dot(rho, F_RV) > VT(0)) || sl.depth >= A.max_depth) {
           end_transition(sl);
           goto next_transition;
         }
@@ -381,25 +425,20 @@ template <int PREC, int NDET, int SLOTS>
 struct NutsSmem {
   using DT = typename std::conditional<PREC == SHARPY_FP64, double, float>::type;
   using MT = typename MomType<PREC>::type;
-  NutsShared<SLOTS> S;
+  NutsShared<SLOTS, DT> S;
   SweepCoef sc[SLOTS];
   EpiCoef<DT> ec[SLOTS];
   MT mom[SLOTS][NDET * kNMom * 2];
 };
 
-// Eight slots: registers capped for two CTAs per SM; wider CTAs run one per SM.
-template <int SLOTS>
-struct NutsMinBlocks {
-  static constexpr int value = SLOTS == 8 ? 2 : 1;
-};
-
 template <int PREC, int NDET, int SLOTS>
-__global__ void __launch_bounds__(kNutsWarps * 32, NutsMinBlocks<SLOTS>::value) nuts_kernel(NutsArgs A) {
+__global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(NutsArgs A) {
   using DT = typename std::conditional<PREC == SHARPY_FP64, double, float>::type;
+  using VT = DT;
   using MT = typename MomType<PREC>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   NutsSmem<PREC, NDET, SLOTS>& SM = *reinterpret_cast<NutsSmem<PREC, NDET, SLOTS>*>(smem_raw);
-  NutsShared<SLOTS>& S = SM.S;
+  NutsShared<SLOTS, VT>& S = SM.S;
   SweepCoef* sc = SM.sc;
   EpiCoef<DT>* ec = SM.ec;
   auto& mom = SM.mom;
@@ -407,38 +446,41 @@ __global__ void __launch_bounds__(kNutsWarps * 32, NutsMinBlocks<SLOTS>::value) 
   const int D = A.m.n_dim;
   const bool gw = A.m.model == SHARPY_MODEL_TAYLORF2;
 
-  // metric, its Cholesky factor (diagonal fallback), step size, beta
+  // metric, its Cholesky factor (diagonal fallback; computed in FP64), step size, beta
   if (threadIdx.x == 0) {
+    double mi[kMaxDim][kMaxDim], ch[kMaxDim][kMaxDim];
     for (int i = 0; i < D; ++i)
-      for (int j = 0; j < D; ++j) S.minv[i][j] = A.minv ? A.minv[i * D + j] : (i == j ? 1.0 : 0.0);
+      for (int j = 0; j < D; ++j) mi[i][j] = A.minv ? A.minv[i * D + j] : (i == j ? 1.0 : 0.0);
     bool ok = true;
     for (int j = 0; j < D && ok; ++j) {
-      for (int i = 0; i < D; ++i) S.chol[i][j] = 0.0;
-      double d = S.minv[j][j];
-      for (int k = 0; k < j; ++k) d -= S.chol[j][k] * S.chol[j][k];
+      for (int i = 0; i < D; ++i) ch[i][j] = 0.0;
+      double d = mi[j][j];
+      for (int k = 0; k < j; ++k) d -= ch[j][k] * ch[j][k];
       if (!(d > 0.0) || !isfinite(d)) {
         ok = false;
         break;
       }
-      S.chol[j][j] = sqrt(d);
+      ch[j][j] = sqrt(d);
       for (int i = j + 1; i < D; ++i) {
-        double t = S.minv[i][j];
-        for (int k = 0; k < j; ++k) t -= S.chol[i][k] * S.chol[j][k];
-        S.chol[i][j] = t / S.chol[j][j];
+        double t = mi[i][j];
+        for (int k = 0; k < j; ++k) t -= ch[i][k] * ch[j][k];
+        ch[i][j] = t / ch[j][j];
       }
     }
     if (!ok)
       for (int i = 0; i < D; ++i)
         for (int j = 0; j < D; ++j) {
-          double dii = S.minv[i][i] > 0.0 && isfinite(S.minv[i][i]) ? S.minv[i][i] : 1.0;
-          S.minv[i][j] = i == j ? dii : 0.0;
-          S.chol[i][j] = i == j ? sqrt(dii) : 0.0;
+          double dii = mi[i][i] > 0.0 && isfinite(mi[i][i]) ? mi[i][i] : 1.0;
+          mi[i][j] = i == j ? dii : 0.0;
+          ch[i][j] = i == j ? sqrt(dii) : 0.0;
         }
     bool ident = true, diag = true;
     for (int i = 0; i < D; ++i)
       for (int j = 0; j < D; ++j) {
-        if (i != j && S.minv[i][j] != 0.0) diag = false;
-        if (S.minv[i][j] != (i == j ? 1.0 : 0.0)) ident = false;
+        if (i != j && mi[i][j] != 0.0) diag = false;
+        if (mi[i][j] != (i == j ? 1.0 : 0.0)) ident = false;
+        S.minv[i][j] = (VT)mi[i][j];
+        S.chol[i][j] = (VT)ch[i][j];
       }
     S.metric_kind = ident ? METRIC_IDENTITY : (diag ? METRIC_DIAGONAL : METRIC_DENSE);
     double lpc = 0.0;
@@ -458,7 +500,7 @@ __global__ void __launch_bounds__(kNutsWarps * 32, NutsMinBlocks<SLOTS>::value) 
   }
   __syncthreads();
 
-  Slot sl;
+  Slot<VT> sl;
   bool active = false;
   if (warp == 0 && lane < SLOTS) {
     Nuts<PREC, NDET, SLOTS> nu(A, S, lane);
@@ -469,8 +511,8 @@ __global__ void __launch_bounds__(kNutsWarps * 32, NutsMinBlocks<SLOTS>::value) 
     sl.st_depth = sl.st_leap = sl.st_div = 0;
     if (sl.pid < A.n) {
       for (int i = 0; i < D; ++i) {
-        nu.V(F_PTH, i) = A.theta[sl.pid * D + i];
-        nu.V(F_PGL, i) = A.grad[sl.pid * D + i];
+        nu.X(P_P, i) = A.theta[sl.pid * D + i];
+        nu.V(F_PGL, i) = (VT)A.grad[sl.pid * D + i];
       }
       sl.lnl_p = A.lnl[sl.pid];
       sl.done = 0;
@@ -493,18 +535,22 @@ __global__ void __launch_bounds__(kNutsWarps * 32, NutsMinBlocks<SLOTS>::value) 
     __syncthreads();
     if (!S.alive) break;
     // (A) prologues (GW) or direct evaluations (Gaussian mixture)
-    double gl_new[kMaxDim], glp_new[kMaxDim], lp_new = 0.0;
+    VT gl_new[kMaxDim], glp_new[kMaxDim];
+    double lp_new = 0.0;
     if (warp == 0 && lane < SLOTS && S.pending[lane]) {
       Nuts<PREC, NDET, SLOTS> nu(A, S, lane);
       double x[kMaxDim];
-      for (int i = 0; i < D; ++i) x[i] = nu.V(F_NTH, i);
-      if (gw)
+      for (int i = 0; i < D; ++i) x[i] = nu.X(P_N, i);
+      if (gw) {
         prologue<DT, true, PREC == SHARPY_MIXED_SPLIT>(A.m, A.ev, x, sc[lane], ec[lane]);
-      else
-        gaussmix(A.m, x, &sl.lnl_new, gl_new);
+      } else {
+        double g[kMaxDim];
+        gaussmix(A.m, x, &sl.lnl_new, g);
+        for (int i = 0; i < D; ++i) gl_new[i] = (VT)g[i];
+      }
     }
     __syncthreads();
-    // (B) sweeps: warp w sweeps slot w
+    // (B) sweeps: warp w sweeps slots w, w + kNutsWarps, ...
     if (gw) {
       for (int slot = warp; slot < SLOTS; slot += kNutsWarps) {
         MT* mw = mom[slot];
@@ -518,7 +564,7 @@ __global__ void __launch_bounds__(kNutsWarps * 32, NutsMinBlocks<SLOTS>::value) 
     if (warp == 0 && lane < SLOTS && S.pending[lane]) {
       Nuts<PREC, NDET, SLOTS> nu(A, S, lane);
       double x[kMaxDim];
-      for (int i = 0; i < D; ++i) x[i] = nu.V(F_NTH, i);
+      for (int i = 0; i < D; ++i) x[i] = nu.X(P_N, i);
       if (gw) {
         double gph[SHARPY_NPHYS];
         sl.lnl_new = NAN;
@@ -526,12 +572,12 @@ __global__ void __launch_bounds__(kNutsWarps * 32, NutsMinBlocks<SLOTS>::value) 
           epilogue<DT, true>(A.ev, sc[lane], ec[lane], mom[lane], &sl.lnl_new, gph);
           sl.st_bins += (double)(sc[lane].kisco + 1) * A.ev.n_det;
         }
-        for (int i = 0; i < D; ++i) gl_new[i] = sc[lane].ok ? gph[A.m.phys[i]] : NAN;
+        for (int i = 0; i < D; ++i) gl_new[i] = sc[lane].ok ? (VT)gph[A.m.phys[i]] : (VT)NAN;
       }
       lp_new = nu.prior(x, glp_new);
       if (!isfinite(sl.lnl_new)) sl.lnl_new = -INFINITY;  // rejected leaf (U = +inf)
       for (int i = 0; i < D; ++i)
-        if (!isfinite(gl_new[i])) gl_new[i] = 0.0;
+        if (!isfinite(gl_new[i])) gl_new[i] = VT(0);
       bool more = nu.advance(sl, true, gl_new, lp_new, glp_new);
       S.pending[lane] = more ? 1 : 0;
     }
@@ -540,8 +586,8 @@ __global__ void __launch_bounds__(kNutsWarps * 32, NutsMinBlocks<SLOTS>::value) 
   if (warp == 0 && lane < SLOTS && sl.pid < A.n) {
     Nuts<PREC, NDET, SLOTS> nu(A, S, lane);
     for (int i = 0; i < D; ++i) {
-      A.theta[sl.pid * D + i] = nu.V(F_PTH, i);
-      A.grad[sl.pid * D + i] = nu.V(F_PGL, i);
+      A.theta[sl.pid * D + i] = nu.X(P_P, i);
+      A.grad[sl.pid * D + i] = (double)nu.V(F_PGL, i);
     }
     A.lnl[sl.pid] = sl.lnl_p;
     if (A.stats) {
@@ -557,7 +603,6 @@ __global__ void __launch_bounds__(kNutsWarps * 32, NutsMinBlocks<SLOTS>::value) 
   }
 }
 
-
 // Launch helper for one (precision, detector count); the slot count is picked
 // by the caller. Defined in nuts_inst.cu, compiled once per combination.
 int launch_nuts(int precision, int ndet, int slots, const NutsArgs& A, cudaStream_t s);
@@ -571,7 +616,6 @@ int launch_nuts_impl(int slots, const NutsArgs& A, cudaStream_t s) {
     kernel<<<grid, kNutsWarps * 32, bytes, s>>>(A);
     return cudaGetLastError() == cudaSuccess ? SHARPY_OK : SHARPY_ECUDA;
   };
-  if (slots == 32) return go(nuts_kernel<P, ND, 32>, 32, sizeof(NutsSmem<P, ND, 32>));
   if (slots == 16) return go(nuts_kernel<P, ND, 16>, 16, sizeof(NutsSmem<P, ND, 16>));
   return go(nuts_kernel<P, ND, 8>, 8, sizeof(NutsSmem<P, ND, 8>));
 }

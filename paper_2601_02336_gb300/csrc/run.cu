@@ -85,18 +85,20 @@ extern "C" int sharpy_smc_run(sharpy_ctx* c, const sharpy_smc_options* o, uint64
   double* cov = sc + 8;
   double* rec = cov + D * D;
   int out = SHARPY_OK;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evr = nullptr;
   auto fail = [&](int code) {
     cudaFreeAsync(buf, s);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
+    if (evr) cudaEventDestroy(evr);
     return code;
   };
   if (cudaMemsetAsync(beta_state, 0, sizeof(double), s) != cudaSuccess) return fail(SHARPY_ECUDA);
   if ((rc = sharpy_reset_evidence(c, stream))) return fail(rc);
   if ((rc = sharpy_prior_sample(c, n, th, key, 0, stream))) return fail(rc);
   if ((rc = sharpy_loglike_grad(c, n, th, ll, gr, o->precision, stream))) return fail(rc);
-  if (o->timing && (cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess))
+  if (o->timing && (cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess ||
+                    cudaEventCreate(&evr) != cudaSuccess))
     return fail(SHARPY_ECUDA);
   double beta = 0.0;
   int t = 0;
@@ -104,6 +106,7 @@ extern "C" int sharpy_smc_run(sharpy_ctx* c, const sharpy_smc_options* o, uint64
     ++t;
     double u0, u1;
     uniform2(key, 0u, (uint32_t)t, RNG_RESAMPLE, 0u, &u0, &u1);
+    if (o->timing) cudaEventRecord(evr, s);
     rc = enqueue_stage(c, n, th, ll, gr, beta_state, 0.0, o->alpha, u0, beta_next, dlnz, ess, nullptr, cov,
                        beta_state, s);
     if (rc) return fail(rc);
@@ -133,9 +136,13 @@ extern "C" int sharpy_smc_run(sharpy_ctx* c, const sharpy_smc_options* o, uint64
       g.n_divergent = (int)r[7];
       g.pad = 0;
       g.active_bins = r[8];
-      float ms = 0.0f;
-      if (o->timing) cudaEventElapsedTime(&ms, ev0, ev1);
+      float ms = 0.0f, rms = 0.0f;
+      if (o->timing) {
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        cudaEventElapsedTime(&rms, evr, ev0);
+      }
       g.nuts_ms = ms;
+      g.reweight_ms = rms;
     }
     beta = r[0];
     if (!std::isfinite(beta)) return fail(SHARPY_ENONFINITE);
@@ -147,6 +154,7 @@ extern "C" int sharpy_smc_run(sharpy_ctx* c, const sharpy_smc_options* o, uint64
   cudaFreeAsync(buf, s);
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
+  if (evr) cudaEventDestroy(evr);
   int ns = 0;
   if ((rc = sharpy_log_evidence(c, lnz, &ns))) return rc;
   if (n_stages) *n_stages = ns;

@@ -67,8 +67,8 @@ static __device__ EssSums ess_sums(const double* lnl, int64_t n, double mx, doub
 // increment (Eq. 6). ESS decreases with db and S2(db) = S1(2 db), so one FP32
 // pass over the geometric grid db_m = hi 2^-m (m = -1..kGrid-2) brackets the
 // root within a factor of two; a Newton iteration on g(db) = 2 ln S1 - ln S2 -
-// ln(alpha N) in FP64, safeguarded by that bracket, then closes it to adjacent
-// doubles. Writes W = e^{db (lnL - max)}, the integer prefix sums C of
+// ln(alpha N) in FP64, safeguarded by that bracket, then locates the root to
+// ~1e-13 relative and keeps the largest evaluated db with ESS >= alpha N. Writes W = e^{db (lnL - max)}, the integer prefix sums C of
 // floor(W 2^32), the ESS, dlnz, beta_next, the covariance, and updates ln Z.
 constexpr int kGrid = 54;
 constexpr int kGridChunk = 9;
@@ -141,21 +141,30 @@ reweight_kernel(int64_t n, const double* __restrict__ lnl, const double* __restr
         lo = (k == 3) ? 0.0 : 0.5 * lo;
       }
       double x = lo > 0.0 ? sqrt(lo * up) : 0.5 * up;
-      for (int it = 0; it < 200; ++it) {
+      // Newton on g inside [lo, up] until the step falls below 1e-13 relative:
+      // g itself is only known to ~1e-15 (logs of large sums), so closer than
+      // that the iteration would wander inside rounding noise. The result is the
+      // root to ~1e-13 relative (the oracle bisects to adjacent doubles).
+      for (int it = 0; it < 60; ++it) {
         EssSums sm = ess_sums(lnl, n, mx, x, red);
         double g = 2.0 * log(sm.s1) - log(sm.s2) - lt;
         if (g >= 0.0)
           lo = x;
         else
           up = x;
-        // Newton step on g; g' = 2 (S1x/S1 - S2x/S2)
         double gp = 2.0 * (sm.s1x / sm.s1 - sm.s2x / sm.s2);
         double xn = x - g / gp;
         if (!(xn > lo && xn < up)) xn = 0.5 * (lo + up);
-        // once Newton moves by an ulp or two, probe the neighbouring double so the
-        // bracket closes to adjacent doubles
-        if (fabs(xn - x) <= 4.440892098500626e-16 * fabs(x)) xn = (g >= 0.0) ? nextafter(x, up) : nextafter(x, lo);
-        if (!(xn > lo && xn < up)) break;  // lo and up are adjacent doubles
+        if (fabs(xn - x) <= 1e-13 * x || !(up - lo > 1e-13 * up)) {
+          // converged; if Newton approached from above, lo may still be far below:
+          // evaluate just under the lowest point known to be above the root
+          const double xb = up * (1.0 - 2e-13);
+          if (xb > lo && up - lo > 2e-13 * up) {
+            EssSums sb = ess_sums(lnl, n, mx, xb, red);
+            if (2.0 * log(sb.s1) - log(sb.s2) - lt >= 0.0) lo = xb;
+          }
+          break;
+        }
         x = xn;
       }
       if (threadIdx.x == 0) sh_db = lo;

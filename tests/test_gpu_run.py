@@ -65,7 +65,7 @@ def test_run_fp64_vs_oracle():
     for seed in range(R):
         r = oracle.smc_run(model, ev, 256, 0.5, 2, 5, 1, 0.5, key=40 + seed)
         g = ctx.smc_run(256, 0.5, 2, 5, 1, 0.5, key=40 + seed, precision="fp64")
-        assert g[3][0]["beta"] == pytest.approx(r[3][0]["beta"], rel=1e-12)
+        assert g[3][0]["beta"] == pytest.approx(r[3][0]["beta"], rel=1e-11)
         assert g[3][0]["dlnz"] == pytest.approx(r[3][0]["dlnz"], rel=1e-9, abs=1e-9)
         ref.append(r[0])
         got.append(g[0])

