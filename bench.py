@@ -155,6 +155,164 @@ def run_reference(args):
     return 0
 
 
+def _active_bins(w, th):
+    """(bins with f_k <= f_ISCO) x detectors per parameter vector (reporting only)."""
+    from paper_2601_02336_gb300 import inputs
+    tsun = 4.925491025543576e-6
+    ph = np.tile(np.array(w.fixed, dtype=np.float64), (th.shape[0], 1))
+    ph[:, w.phys] = th
+    mc, q = ph[:, inputs.MC], ph[:, inputs.Q]
+    eta = q / (1.0 + q) ** 2
+    m = mc * eta ** -0.6
+    fisco = 1.0 / (6.0 ** 1.5 * math.pi * m * tsun)
+    k = np.clip(np.floor((fisco - w.f_min) / w.df), -1, w.n_bins - 1)
+    return (k + 1) * w.n_det
+
+
+def main_loglike(args):
+    """sharpy_loglike_grad throughput (one call = ln L + gradient of N particles)
+    on two parameter sets of a workload: prior draws and a Gaussian ball around
+    the injection (sigma = 1e-3 x prior width); FP64, mixed and split paths;
+    the oracle's rate on 64 of the ball's vectors (1 thread and all threads) and
+    the mixed path's largest |d lnL| against it. One JSON line per workload."""
+    import torch
+
+    import oracle
+    from paper_2601_02336_gb300 import api, inputs
+    from paper_2601_02336_gb300._lib import lib
+    from tests import helpers
+
+    torch.cuda.set_device(0)
+    w = inputs.WORKLOADS[args.workload]()
+    ctx, th_inj, data = api.make_event(w, seed=0)
+    n = max(w.n_particles, 2048)
+    sets = {"prior": inputs.prior_draws(w, n, 1), "ball": inputs.ball(w, th_inj, n, 2, rel=1e-3)}
+    peaks = (C.c_double * 3)()
+    lib().sharpy_probe_peaks(0, peaks)
+    stream = torch.cuda.current_stream()
+    out = {"mode": "loglike", "workload": w.name, "n_bins": w.n_bins, "n_det": w.n_det, "particles_per_call": n,
+           "fp32_peak_tflops": peaks[0], "fp64_peak_tflops": peaks[1], "sets": {}}
+    for name, th in sets.items():
+        t = torch.tensor(th, dtype=torch.float64, device="cuda")
+        act = float(_active_bins(w, th).mean())
+        row = {"active_bin_det_per_eval": act}
+        for prec in ("fp64", "mixed", "split"):
+            for _ in range(2):
+                ctx.loglike_grad(t, prec)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 5
+            e0.record(stream)
+            for _ in range(reps):
+                ctx.loglike_grad(t, prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            wk = WORK[prec]
+            tfl = n * act * wk["flop"] / (ms * 1e-3) / 1e12
+            peak = peaks[1] if wk["pipe"] == "fp64" else peaks[0]
+            row[prec] = {"evals_per_s": n / (ms * 1e-3), "ms_per_call": ms, "pipe": wk["pipe"],
+                         "achieved_tflops": tfl, "frac": tfl / peak}
+        out["sets"][name] = row
+    # oracle on 64 vectors of the ball set, and the mixed path's error against it
+    oracle.build()
+    model = helpers.oracle_model(w)
+    ev, _, odata = helpers.make_event(w, seed=0)
+    sub = sets["ball"][:64]
+    cores = os.cpu_count()
+    rates = {}
+    for threads in (1, cores):
+        prev = oracle.set_threads(threads)
+        t0 = time.perf_counter()
+        lref, gref = oracle.loglike(model, ev, sub)
+        rates[threads] = len(sub) / (time.perf_counter() - t0)
+        oracle.set_threads(prev)
+    # the same arrays on both sides: the oracle's event staged into a second context
+    ctx2 = api.Context.from_workload(w)
+    ctx2.set_data(odata, inputs.psd_array(w), w.f_min, w.df, inputs.detectors(w))
+    lm, gm = ctx2.loglike_grad(torch.tensor(sub, dtype=torch.float64, device="cuda"), "mixed")
+    out["oracle"] = {"evals_per_s_1_thread": rates[1], "evals_per_s_all": rates[cores], "cores": cores,
+                     "sample": "64 vectors of the ball set"}
+    out["mixed_max_abs_dlnl_vs_oracle"] = float(np.max(np.abs(lm.cpu().numpy() - lref)))
+    print(json.dumps(out))
+    return 0
+
+
+def main_batch(args):
+    """64 uneven events (4/8/16/32 s segments, 512-8192 particles, NUTS depth 8)
+    sampled together by the batched driver: one step = one batched run of all
+    64 events from their prior draws to beta = 1."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2601_02336_gb300 import api, inputs, multirank
+
+    rank, world, local = multirank.env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ws = inputs.batch64()
+    base = multirank.event_seed(rank) * 1000
+    ctxs = [api.make_event(w, seed=base + i, device=local)[0] for i, w in enumerate(ws)]
+    w0 = ws[0]
+    b = api.Batch(ctxs, [w.n_particles for w in ws], w0.alpha, w0.n_mut, w0.max_depth, w0.metric, w0.eps_scale,
+                  precision=args.precision, max_stages=500)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for i in range(args.warmup):
+        b.run([multirank.run_key(10_000 + 100 * i, rank, e) for e in range(len(ws))])
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    evals, bins, rounds, step_ms, lnzs = 0.0, 0.0, [], [], []
+    for k in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res, nr = b.run([multirank.run_key(20_000 + 100 * k, rank, e) for e in range(len(ws))])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        evals += sum(r["n_leapfrog"] for r in res)
+        bins += sum(r["active_bins"] for r in res)
+        rounds.append(nr)
+        lnzs.append([r["lnz"] for r in res])
+    barrier()
+    clk = clocks.stop()
+    t_rank = sum(step_ms)
+    t_max = multirank.reduce_scalar(t_rank, "max", world, device="cuda")
+    total = multirank.reduce_scalar(evals, "sum", world, device="cuda")
+    n_ev = len(ws) * args.steps * world
+    if rank == 0:
+        wk = WORK[args.precision]
+        out = {"metric": METRIC, "value": total / (t_max * 1e-3), "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": {"mixed": "f32+f64", "split": "f32 (f64 per particle)", "fp64": "f64"}[args.precision],
+               "data": "synthetic",
+               "config": {"workload": "batch64: 64 events of the 11-D TaylorF2 model, segments 4/8/16/32 s "
+                                      "(16 each, 20-1024 Hz at 1/T), 512-8192 particles (log-uniform), NUTS depth 8; "
+                                      "one step = one batched run of all 64 events",
+                          "precision": args.precision, "l2": "flushed (256 MB write) between steps",
+                          "particles": int(sum(w.n_particles for w in ws)), "slots": b.slots,
+                          "rounds_per_run": rounds},
+               "events_per_hour": n_ev / (t_max * 1e-3) * 3600.0,
+               "round_ms": t_max / max(sum(rounds), 1),
+               "achieved_tflops_whole_step": bins * wk["flop"] / (t_rank * 1e-3) / 1e12,
+               "gpu_launches": None, "clocks": clk,
+               "lnz_first_events": [float(x) for x in lnzs[0][:4]]}
+        print(json.dumps(out))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -165,9 +323,15 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="bbh11", choices=["tiny", "bbh11", "bbh11_long", "bns", "batch64"])
+    ap.add_argument("--mode", default="smc", choices=["smc", "loglike"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "loglike":
+        return main_loglike(args)
+    if args.workload == "batch64":
+        return main_batch(args)
 
     import torch
     import torch.distributed as dist

@@ -181,8 +181,9 @@ int sharpy_nuts_mutate(sharpy_ctx* ctx, int64_t n, double beta, double* theta, d
                        sharpy_stream stream);
 
 /* One tempering step (Sec. 3, Eqs. 4-8): the increment dbeta solving
-   ESS = alpha N by 100 bisection steps (or dbeta = 1 - beta_prev if that
-   already keeps ESS >= alpha N), weights W_i = exp(dbeta (lnL_i - max)),
+   ESS = alpha N (the largest FP64-verified dbeta with ESS >= alpha N, within
+   1e-12 relative of the root; or dbeta = 1 - beta_prev if that already keeps
+   ESS >= alpha N), weights W_i = exp(dbeta (lnL_i - max)),
    dlnz = logsumexp(dbeta lnL) - ln N (also added to the context's ln Z),
    the weighted covariance of theta under W (cov [D][D], or NULL), then
    systematic resampling with uniform u in [0,1) (see
@@ -236,6 +237,50 @@ int sharpy_log_evidence(sharpy_ctx* ctx, double* lnz, int* n_stages);
 int sharpy_smc_run(sharpy_ctx* ctx, const sharpy_smc_options* opt, uint64_t key, double* lnz,
                    int* n_stages, double* theta_out, double* lnl_out, sharpy_stage* stages,
                    sharpy_stream stream);
+
+/* Batched SMC over many events (Sec. 3 applied to each event independently;
+   the paper runs one event at a time). Every event keeps its own tempering
+   ladder, particles, metric and evidence; each stage "round" advances all
+   events that have not reached beta = 1 with one reweight launch (one
+   thread-block cluster per event), one resampling pass and ONE persistent
+   NUTS launch over every particle of every event, its CTAs ordered by event
+   cost. The round is captured once as a CUDA graph and replayed; the host
+   reads the events' active flags every few rounds only.
+   events: n_events contexts with data staged (sharpy_set_data), all with the
+   same model kind and detector count; n_particles[e]: particles of event e
+   (HOST array); opt: alpha, n_mut, max_depth, metric, eps_scale, precision,
+   max_stages as in sharpy_smc_run (opt->n_particles and opt->timing are
+   ignored). The contexts must outlive the batch. Allocates the batch's device
+   memory (particles of all events, stage scratch, records). Synchronous. */
+typedef struct sharpy_batch sharpy_batch;
+typedef struct {
+  double lnz;          /* ln Z of the event (Sec. 3.1, Eq. 8)                    */
+  double beta;         /* final beta (1 unless max_stages was reached)           */
+  double n_leapfrog;   /* leapfrogs (likelihood+gradient evaluations), all stages */
+  double active_bins;  /* sum over those evaluations of (bins below f_ISCO) x detectors */
+  int n_stages;
+  int pad;
+} sharpy_batch_result;
+int sharpy_batch_create(sharpy_batch** out, sharpy_ctx* const* events, int n_events, const int64_t* n_particles,
+                        const sharpy_smc_options* opt);
+void sharpy_batch_destroy(sharpy_batch* b);
+/* Run every event from its prior draw to beta = 1: event e uses keys[e]
+   exactly as sharpy_smc_run(events[e], opt, keys[e]) does, and gives the same
+   particles and ln Z bit for bit. results: HOST array [n_events]; rounds:
+   HOST, optional (stage rounds replayed). Returns SHARPY_ETIMEOUT if some
+   event did not reach beta = 1 within max_stages. Synchronous. */
+int sharpy_batch_run(sharpy_batch* b, const uint64_t* keys, sharpy_batch_result* results, int* rounds,
+                     sharpy_stream stream);
+/* Particles of event e after the last run: theta [N_e][D], lnl [N_e]
+   (device, either may be NULL). Stream-ordered. */
+int sharpy_batch_particles(sharpy_batch* b, int e, double* theta, double* lnl, sharpy_stream stream);
+/* Stage records of event e from the last run (HOST array of `cap` entries;
+   *n = stages written). nuts_ms and reweight_ms are 0. Synchronous. */
+int sharpy_batch_stages(sharpy_batch* b, int e, sharpy_stage* stages, int cap, int* n);
+/* Slot count (particles per NUTS CTA: 8, 16 or 32) the batch's launches
+   use, picked by timing each candidate on the batch's own first stage (0
+   before the first run). The results do not depend on it. */
+int sharpy_batch_slots(sharpy_batch* b);
 
 /* Measurement helper: FP32 FMA TFLOP/s, FP64 FMA TFLOP/s and SFU sin+cos
    Gop/s of `device` from register-only kernels (out[3], host). Used as the

@@ -97,6 +97,7 @@ _SIGS = {
     "ref_f_isco": (C.c_double, [C.c_double] * 2),
     "ref_waveform": (C.c_int, [_P(Model), _P(Event), _D, _D]),
     "ref_loglike": (C.c_int, [_P(Model), _P(Event), C.c_int64, _D, _D, _D]),
+    "ref_set_threads": (C.c_int, [C.c_int]),
     "ref_prior_sample": (C.c_int, [_P(Model), C.c_int64, _D, C.c_uint64, C.c_uint32]),
     "ref_prior_logpdf_grad": (C.c_int, [_P(Model), C.c_int64, _D, _D, _D]),
     "ref_nuts_mutate": (C.c_int, [_P(Model), _P(Event), C.c_int64, C.c_double, _D, _D, _D, _D,
@@ -234,6 +235,11 @@ def waveform(model, event: EventHolder, theta):
     h = np.zeros((event.ev.n_det, event.ev.n_bins, 2))
     _check(lib().ref_waveform(C.byref(model), C.byref(event.ev), _dp(theta), _dp(h)), "waveform")
     return h
+
+
+def set_threads(n):
+    """OpenMP threads of the particle loops (results do not depend on it); returns the previous value."""
+    return lib().ref_set_threads(int(n))
 
 
 def loglike(model, event, theta, grad=True):

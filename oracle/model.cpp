@@ -8,6 +8,10 @@
 #include "dual.h"
 #include "oracle.h"
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 namespace oracle {
 
 // Physical constants (CODATA / IAU nominal values).
@@ -363,6 +367,17 @@ int ref_waveform(const ref_model* m, const ref_event* ev, const double* theta, d
     }
   }
   return 0;
+}
+
+int ref_set_threads(int n) {
+#ifdef _OPENMP
+  const int prev = omp_get_max_threads();
+  if (n > 0) omp_set_num_threads(n);
+  return prev;
+#else
+  (void)n;
+  return 1;
+#endif
 }
 
 int ref_loglike(const ref_model* m, const ref_event* ev, int64_t n, const double* theta, double* lnl,

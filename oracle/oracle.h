@@ -139,6 +139,10 @@ double ref_f_isco(double mc, double q);
 /* Detector-frame strain h_a(f_k) of one parameter vector theta (free dims). */
 int ref_waveform(const ref_model* m, const ref_event* ev, const double* theta, double* h);
 
+/* Number of OpenMP threads the particle loops use (timing only: every result
+   is independent of it). Returns the previous setting. */
+int ref_set_threads(int n);
+
 /* ln L (and its gradient if grad != NULL) of N parameter vectors [N][D]. */
 int ref_loglike(const ref_model* m, const ref_event* ev, int64_t n, const double* theta,
                 double* lnl, double* grad);

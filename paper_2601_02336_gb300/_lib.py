@@ -53,6 +53,11 @@ class Stage(C.Structure):
                 ("reweight_ms", C.c_double)]
 
 
+class BatchResult(C.Structure):
+    _fields_ = [("lnz", C.c_double), ("beta", C.c_double), ("n_leapfrog", C.c_double),
+                ("active_bins", C.c_double), ("n_stages", C.c_int), ("pad", C.c_int)]
+
+
 _VP = C.c_void_p
 _CTX = C.c_void_p
 _SIGS = {
@@ -75,6 +80,14 @@ _SIGS = {
     "sharpy_log_evidence": (C.c_int, [_CTX, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "sharpy_smc_run": (C.c_int, [_CTX, C.POINTER(SmcOptions), C.c_uint64, C.POINTER(C.c_double),
                                  C.POINTER(C.c_int), _VP, _VP, C.POINTER(Stage), _VP]),
+    "sharpy_batch_create": (C.c_int, [C.POINTER(_VP), C.POINTER(_CTX), C.c_int, C.POINTER(C.c_int64),
+                                      C.POINTER(SmcOptions)]),
+    "sharpy_batch_destroy": (None, [_VP]),
+    "sharpy_batch_run": (C.c_int, [_VP, C.POINTER(C.c_uint64), C.POINTER(BatchResult),
+                                   C.POINTER(C.c_int), _VP]),
+    "sharpy_batch_particles": (C.c_int, [_VP, C.c_int, _VP, _VP, _VP]),
+    "sharpy_batch_stages": (C.c_int, [_VP, C.c_int, C.POINTER(Stage), C.c_int, C.POINTER(C.c_int)]),
+    "sharpy_batch_slots": (C.c_int, [_VP]),
     "sharpy_get_status": (C.c_int, [_CTX]),
     "sharpy_clear_status": (C.c_int, [_CTX]),
     "sharpy_error_string": (C.c_char_p, [C.c_int]),

@@ -12,8 +12,8 @@ import numpy as np
 import torch
 
 from . import inputs
-from ._lib import (FP64, MIXED, MIXED_SPLIT, MODEL_GAUSSMIX, MODEL_TAYLORF2, Config, Detector, NutsStats,
-                   SmcOptions, Stage, check, lib)
+from ._lib import (FP64, MIXED, MIXED_SPLIT, MODEL_GAUSSMIX, MODEL_TAYLORF2, BatchResult, Config, Detector,
+                   NutsStats, SmcOptions, Stage, check, lib)
 
 PRECISION = {"fp64": FP64, "mixed": MIXED, "split": MIXED_SPLIT}
 STATS_DTYPE = np.dtype([("accept_sum", "<f8"), ("active_bins", "<f8"), ("depth_sum", "<i4"),
@@ -201,6 +201,67 @@ class Context:
 
     def clear_status(self):
         check(lib().sharpy_clear_status(self._h), "sharpy_clear_status")
+
+
+class Batch:
+    """Many events sampled together (sharpy_batch_*): one persistent NUTS launch
+    and one reweight launch per stage round cover every event still tempering;
+    the rounds replay a captured CUDA graph. Keeps references to the contexts."""
+
+    def __init__(self, contexts, n_particles, alpha, n_mut, max_depth, metric, eps_scale, precision="mixed",
+                 max_stages=500):
+        self.contexts = list(contexts)
+        self.n_particles = [int(n) for n in n_particles]
+        if len(self.n_particles) != len(self.contexts):
+            raise ValueError("one particle count per context")
+        self.max_stages = max_stages
+        o = SmcOptions(0, alpha, n_mut, max_depth, metric, eps_scale, _prec(precision), max_stages, 0, 0)
+        ne = len(self.contexts)
+        hs = (C.c_void_p * ne)(*[c._h.value for c in self.contexts])
+        ns = (C.c_int64 * ne)(*self.n_particles)
+        h = C.c_void_p()
+        check(lib().sharpy_batch_create(C.byref(h), hs, ne, ns, C.byref(o)), "sharpy_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().sharpy_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, keys):
+        """Run every event to beta = 1. Returns (list of result dicts, rounds)."""
+        ne = len(self.contexts)
+        if len(keys) != ne:
+            raise ValueError("one key per event")
+        k = (C.c_uint64 * ne)(*[int(x) for x in keys])
+        res = (BatchResult * ne)()
+        rounds = C.c_int()
+        check(lib().sharpy_batch_run(self._h, k, res, C.byref(rounds), _stream()), "sharpy_batch_run")
+        out = [dict((f, getattr(res[e], f)) for f, _ in BatchResult._fields_ if f != "pad") for e in range(ne)]
+        return out, rounds.value
+
+    def particles(self, e):
+        c = self.contexts[e]
+        th = torch.empty((self.n_particles[e], c.n_dim), dtype=torch.float64, device=f"cuda:{c.device}")
+        ll = torch.empty(self.n_particles[e], dtype=torch.float64, device=th.device)
+        check(lib().sharpy_batch_particles(self._h, e, _ptr(th), _ptr(ll), _stream()), "sharpy_batch_particles")
+        return th, ll
+
+    def stages(self, e):
+        st = (Stage * self.max_stages)()
+        n = C.c_int()
+        check(lib().sharpy_batch_stages(self._h, e, st, self.max_stages, C.byref(n)), "sharpy_batch_stages")
+        return [dict((f, getattr(st[i], f)) for f, _ in Stage._fields_ if f != "pad") for i in range(n.value)]
+
+    @property
+    def slots(self):
+        return lib().sharpy_batch_slots(self._h)
 
 
 def systematic_resample(w, u):

@@ -44,6 +44,8 @@ struct DevDetector {
   double D[3][3];  // detector tensor (x x^T - y y^T)/2
   float Df[3][3];  // the same in FP32 (antenna patterns of the mixed path)
   double r[3];     // position [m]
+  double rcd[3];   // position / c [s]
+  float rcf[3];    // the same in FP32 (delays of the mixed path)
 };
 
 // Staged event tables (device pointers, SoA), built by sharpy_set_data.
@@ -51,6 +53,7 @@ struct DevEvent {
   int n_det;
   int64_t n_bins;
   double f_min, df;
+  double inv_df;             // 1 / df (k_ISCO guess; the table decides)
   double dd;                 // <d|d> over all bins and detectors
   const double* f;           // [K] f_k
   const double* b64;         // [kNBasis][K] basis functions (FP64)

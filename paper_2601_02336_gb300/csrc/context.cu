@@ -70,6 +70,10 @@ static void detector_geometry(const sharpy_detector& in, DevDetector& out) {
   out.r[0] = kEarthR * cl * co;
   out.r[1] = kEarthR * cl * so;
   out.r[2] = kEarthR * sl;
+  for (int i = 0; i < 3; ++i) {
+    out.rcd[i] = out.r[i] / kClight;
+    out.rcf[i] = (float)out.rcd[i];
+  }
 }
 
 extern "C" {
@@ -225,6 +229,7 @@ int sharpy_set_data(sharpy_ctx* c, int n_det, int64_t n_bins, double f_min, doub
   ev.n_bins = K;
   ev.f_min = f_min;
   ev.df = df;
+  ev.inv_df = 1.0 / df;
   ev.dd = dd + ddc;
   ev.f = c->d_f;
   ev.b64 = c->d_b64;

@@ -26,6 +26,10 @@ struct sharpy_ctx {
   // pinned host staging for small readbacks
   double* h_pinned = nullptr;
   cudaStream_t last_stream = nullptr;
+  // NUTS slot count picked by the autotuner for (tuned_n, tuned_prec)
+  int tuned_slots = 0;
+  int64_t tuned_n = -1;
+  int tuned_prec = -1;
 };
 
 namespace sharpy {

@@ -6,34 +6,38 @@ using namespace sharpy;
 namespace sharpy {
 
 // Defined by the six compilations of nuts_inst.cu.
-int launch_nuts_p0_1(int slots, const NutsArgs& A, cudaStream_t s);
-int launch_nuts_p0_2(int slots, const NutsArgs& A, cudaStream_t s);
-int launch_nuts_p0_3(int slots, const NutsArgs& A, cudaStream_t s);
-int launch_nuts_p1_1(int slots, const NutsArgs& A, cudaStream_t s);
-int launch_nuts_p1_2(int slots, const NutsArgs& A, cudaStream_t s);
-int launch_nuts_p1_3(int slots, const NutsArgs& A, cudaStream_t s);
-int launch_nuts_p2_1(int slots, const NutsArgs& A, cudaStream_t s);
-int launch_nuts_p2_2(int slots, const NutsArgs& A, cudaStream_t s);
-int launch_nuts_p2_3(int slots, const NutsArgs& A, cudaStream_t s);
+int launch_nuts_p0_1(int slots, const NutsArgs& A, unsigned grid, cudaStream_t s);
+int launch_nuts_p0_2(int slots, const NutsArgs& A, unsigned grid, cudaStream_t s);
+int launch_nuts_p0_3(int slots, const NutsArgs& A, unsigned grid, cudaStream_t s);
+int launch_nuts_p1_1(int slots, const NutsArgs& A, unsigned grid, cudaStream_t s);
+int launch_nuts_p1_2(int slots, const NutsArgs& A, unsigned grid, cudaStream_t s);
+int launch_nuts_p1_3(int slots, const NutsArgs& A, unsigned grid, cudaStream_t s);
+int launch_nuts_p2_1(int slots, const NutsArgs& A, unsigned grid, cudaStream_t s);
+int launch_nuts_p2_2(int slots, const NutsArgs& A, unsigned grid, cudaStream_t s);
+int launch_nuts_p2_3(int slots, const NutsArgs& A, unsigned grid, cudaStream_t s);
 
-int launch_nuts(int precision, int ndet, int slots, const NutsArgs& A, cudaStream_t s) {
+int launch_nuts(int precision, int ndet, int slots, const NutsArgs& A, unsigned grid, cudaStream_t s) {
   if (precision == SHARPY_FP64) {
-    if (ndet == 1) return launch_nuts_p0_1(slots, A, s);
-    if (ndet == 2) return launch_nuts_p0_2(slots, A, s);
-    return launch_nuts_p0_3(slots, A, s);
+    if (ndet == 1) return launch_nuts_p0_1(slots, A, grid, s);
+    if (ndet == 2) return launch_nuts_p0_2(slots, A, grid, s);
+    return launch_nuts_p0_3(slots, A, grid, s);
   }
   if (precision == SHARPY_MIXED) {
-    if (ndet == 1) return launch_nuts_p1_1(slots, A, s);
-    if (ndet == 2) return launch_nuts_p1_2(slots, A, s);
-    return launch_nuts_p1_3(slots, A, s);
+    if (ndet == 1) return launch_nuts_p1_1(slots, A, grid, s);
+    if (ndet == 2) return launch_nuts_p1_2(slots, A, grid, s);
+    return launch_nuts_p1_3(slots, A, grid, s);
   }
-  if (ndet == 1) return launch_nuts_p2_1(slots, A, s);
-  if (ndet == 2) return launch_nuts_p2_2(slots, A, s);
-  return launch_nuts_p2_3(slots, A, s);
+  if (ndet == 1) return launch_nuts_p2_1(slots, A, grid, s);
+  if (ndet == 2) return launch_nuts_p2_2(slots, A, grid, s);
+  return launch_nuts_p2_3(slots, A, grid, s);
 }
+// slots: particles per CTA; 0 picks the autotuned count for (n, precision) if
+// the context has one, else the widest count that still gives about two CTAs
+// per SM.
 int enqueue_nuts(sharpy_ctx* c, int64_t n, const double* beta_ptr, double beta, double* theta, double* lnl,
                  double* grad, const double* inv_mass, const double* cov_step, double step, int max_depth,
-                 int n_steps, uint64_t key, uint32_t ctr, int precision, sharpy_nuts_stats* stats, cudaStream_t s) {
+                 int n_steps, uint64_t key, uint32_t ctr, int precision, sharpy_nuts_stats* stats, cudaStream_t s,
+                 int slots) {
   NutsArgs A;
   A.m = c->model;
   A.ev = c->ev;
@@ -52,13 +56,19 @@ int enqueue_nuts(sharpy_ctx* c, int64_t n, const double* beta_ptr, double beta, 
   A.ctr = ctr;
   A.stats = stats;
   A.status = c->d_status;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // widest slot count that still gives about two CTAs per SM
-  const int slots = n >= (int64_t)16 * 2 * sms * 3 / 4 ? 16 : 8;
+  if (!slots && c->tuned_slots && c->tuned_n == n && c->tuned_prec == precision) slots = c->tuned_slots;
+  if (!slots) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    slots = n >= (int64_t)16 * 2 * sms * 3 / 4 ? 16 : 8;
+  }
   const int nd = c->model.model == SHARPY_MODEL_TAYLORF2 ? c->ev.n_det : 1;
-  return launch_nuts(precision, nd, slots, A, s);
+  A.batch = nullptr;
+  A.cta_map = nullptr;
+  A.active = nullptr;
+  A.stage = nullptr;
+  return launch_nuts(precision, nd, slots, A, 0u, s);
 }
 }  // namespace sharpy
 
@@ -77,5 +87,5 @@ extern "C" int sharpy_nuts_mutate(sharpy_ctx* c, int64_t n, double beta, double*
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
   return enqueue_nuts(c, n, nullptr, beta, theta, lnl, grad, inv_mass, nullptr, step, max_depth, n_steps, key,
-                      (uint32_t)ctr, precision, stats, s);
+                      (uint32_t)ctr, precision, stats, s, 0);
 }

@@ -11,8 +11,8 @@ namespace sharpy {
 
 #define SHARPY_CAT2(a, b, c) a##b##_##c
 #define SHARPY_CAT(a, b, c) SHARPY_CAT2(a, b, c)
-int SHARPY_CAT(launch_nuts_p, SHARPY_NUTS_PREC, SHARPY_NUTS_NDET)(int slots, const NutsArgs& A, cudaStream_t s) {
-  return launch_nuts_impl<SHARPY_NUTS_PREC, SHARPY_NUTS_NDET>(slots, A, s);
+int SHARPY_CAT(launch_nuts_p, SHARPY_NUTS_PREC, SHARPY_NUTS_NDET)(int slots, const NutsArgs& A, unsigned grid, cudaStream_t s) {
+  return launch_nuts_impl<SHARPY_NUTS_PREC, SHARPY_NUTS_NDET>(slots, A, grid, s);
 }
 
 }  // namespace sharpy

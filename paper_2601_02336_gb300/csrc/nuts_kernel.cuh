@@ -74,6 +74,13 @@ struct NutsArgs {
   uint32_t ctr;
   sharpy_nuts_stats* stats;
   int* status;
+  // batched driver (null otherwise): CTA b runs block cta_map[b].y of event
+  // cta_map[b].x, whose arguments are batch[cta_map[b].x]; an event's CTAs
+  // return at once while *active == 0, and its counter is *stage << 8
+  const NutsArgs* batch;
+  const int2* cta_map;
+  const int* active;
+  const int* stage;
 };
 
 enum { METRIC_IDENTITY = 0, METRIC_DIAGONAL = 1, METRIC_DENSE = 2 };
@@ -84,6 +91,7 @@ struct NutsShared {
   VT vec[F_COUNT][kMaxDim][SLOTS];
   VT minv[kMaxDim][kMaxDim];
   VT chol[kMaxDim][kMaxDim];
+  long long lokey[kMaxDim], hikey[kMaxDim];  // order keys of the prior box (see okey)
   double eps, beta;
   double lp_const;  // sum of the prior's constant log terms
   int metric_kind;
@@ -100,6 +108,14 @@ __device__ __forceinline__ double vsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float vsqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ void vsincospi(double x, double* s, double* c) { sincospi(x, s, c); }
 __device__ __forceinline__ void vsincospi(float x, float* s, float* c) { sincospif(x, s, c); }
+
+// Order key of a double: for non-NaN x, y, okey(x) < okey(y) implies x < y
+// (and x < y implies okey(x) < okey(y) except for -0 < +0). Lets the box test
+// run on the integer pipes instead of the FP64 one.
+__device__ __forceinline__ long long okey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
 
 template <class VT>
 __device__ __forceinline__ VT logaddexp(VT a, VT b) {
@@ -176,14 +192,16 @@ struct Nuts {
     for (int i = 0; i < D; ++i) k += a[i] * b[i];
     return k;
   }
-  // ln pi (FP64 total) and grad ln pi with the constant terms precomputed
+  // ln pi (FP64 total) and grad ln pi with the constant terms precomputed.
+  // CHECK = false: x is known to lie in the box (it came out of boundary()).
+  template <bool CHECK = true>
   __device__ double prior(const double* x, VT* g) {
     const DevModel& m = A.m;
     double lp = S.lp_const;
     bool inside = true;
     for (int i = 0; i < D; ++i) {
       g[i] = VT(0);
-      if (!(x[i] >= m.lo[i] && x[i] <= m.hi[i])) inside = false;
+      if (CHECK && !(x[i] >= m.lo[i] && x[i] <= m.hi[i])) inside = false;
       if (m.prior[i] == SHARPY_PRIOR_POWER2) {
         const VT xi = (VT)x[i];
         lp += (double)(VT(2) * vlog(xi));
@@ -198,9 +216,15 @@ struct Nuts {
     const DevModel& m = A.m;
     for (int i = 0; i < D; ++i) {
       double x = X(P_N, i);
-      if (!isfinite(x)) return false;
+      const long long b = __double_as_longlong(x);
+      if ((b & 0x7ff0000000000000LL) == 0x7ff0000000000000LL) return false;  // not finite
+      const bool periodic = m.boundary[i] == SHARPY_BOUND_PERIODIC;
+      if (!periodic) {
+        const long long k = okey(x);
+        if (k >= S.lokey[i] && k <= S.hikey[i]) continue;  // inside: nothing to do
+      }
       double lo = m.lo[i], hi = m.hi[i];
-      if (m.boundary[i] == SHARPY_BOUND_PERIODIC) {
+      if (periodic) {
         // lo + ((x - lo) mod w): for |x - lo| < 2w one exact subtraction or
         // addition gives fmod's result; fmod only for larger excursions
         const double w = hi - lo;
@@ -432,17 +456,40 @@ struct NutsSmem {
 };
 
 template <int PREC, int NDET, int SLOTS>
-__global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(NutsArgs A) {
+__global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(const __grid_constant__ NutsArgs P) {
   using DT = typename std::conditional<PREC == SHARPY_FP64, double, float>::type;
   using VT = DT;
   using MT = typename MomType<PREC>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  // this CTA's arguments (its event's, in a batched launch) in shared memory
+  __shared__ __align__(16) NutsArgs A;
+  __shared__ int s_block, s_skip;
+  {
+    const int2 cm = P.batch ? P.cta_map[blockIdx.x] : make_int2(0, (int)blockIdx.x);
+    const NutsArgs* src = P.batch ? P.batch + cm.x : &P;
+    static_assert(sizeof(NutsArgs) % 8 == 0, "NutsArgs is copied as 8-byte words");
+    const unsigned long long* s8 = reinterpret_cast<const unsigned long long*>(src);
+    unsigned long long* d8 = reinterpret_cast<unsigned long long*>(&A);
+    for (int i = threadIdx.x; i < (int)(sizeof(NutsArgs) / 8); i += blockDim.x) d8[i] = s8[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_block = cm.y;
+      s_skip = (A.active && *A.active == 0) ? 1 : 0;
+      if (A.stage) A.ctr = (uint32_t)(*A.stage) << 8;
+    }
+    __syncthreads();
+    if (s_skip) return;
+  }
   NutsSmem<PREC, NDET, SLOTS>& SM = *reinterpret_cast<NutsSmem<PREC, NDET, SLOTS>*>(smem_raw);
   NutsShared<SLOTS, VT>& S = SM.S;
   SweepCoef* sc = SM.sc;
   EpiCoef<DT>* ec = SM.ec;
   auto& mom = SM.mom;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // control warp: warp 0 or 2 by CTA parity, so the serial (FP64-heavy) phases
+  // of two CTAs sharing an SM run on different SM sub-partitions
+  const int cw = (blockIdx.x & 1) << 1;
+  const int sw = (warp - cw) & (kNutsWarps - 1);  // this warp's rank in the sweep order
   const int D = A.m.n_dim;
   const bool gw = A.m.model == SHARPY_MODEL_TAYLORF2;
 
@@ -483,6 +530,10 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(NutsArgs A) {
         S.chol[i][j] = (VT)ch[i][j];
       }
     S.metric_kind = ident ? METRIC_IDENTITY : (diag ? METRIC_DIAGONAL : METRIC_DENSE);
+    for (int i = 0; i < D; ++i) {
+      S.lokey[i] = okey(A.m.lo[i]);
+      S.hikey[i] = okey(A.m.hi[i]);
+    }
     double lpc = 0.0;
     for (int i = 0; i < D; ++i) {
       double lo = A.m.lo[i], hi = A.m.hi[i];
@@ -502,9 +553,9 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(NutsArgs A) {
 
   Slot<VT> sl;
   bool active = false;
-  if (warp == 0 && lane < SLOTS) {
+  if (warp == cw && lane < SLOTS) {
     Nuts<PREC, NDET, SLOTS> nu(A, S, lane);
-    sl.pid = (int64_t)blockIdx.x * SLOTS + lane;
+    sl.pid = (int64_t)s_block * SLOTS + lane;
     sl.t = 0;
     sl.done = 1;
     sl.st_acc = sl.st_bins = 0.0;
@@ -523,7 +574,7 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(NutsArgs A) {
   const long max_ticks = (long)A.n_steps * ((1L << A.max_depth) + 1) + 4;
   for (long tick = 0;; ++tick) {
     // warp 0: any pending evaluation left?
-    if (warp == 0) {
+    if (warp == cw) {
       unsigned any = __ballot_sync(0xffffffffu, lane < SLOTS && S.pending[lane]);
       if (lane == 0) S.alive = any != 0u;
       if (tick > max_ticks && any) {
@@ -537,7 +588,7 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(NutsArgs A) {
     // (A) prologues (GW) or direct evaluations (Gaussian mixture)
     VT gl_new[kMaxDim], glp_new[kMaxDim];
     double lp_new = 0.0;
-    if (warp == 0 && lane < SLOTS && S.pending[lane]) {
+    if (warp == cw && lane < SLOTS && S.pending[lane]) {
       Nuts<PREC, NDET, SLOTS> nu(A, S, lane);
       double x[kMaxDim];
       for (int i = 0; i < D; ++i) x[i] = nu.X(P_N, i);
@@ -552,7 +603,7 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(NutsArgs A) {
     __syncthreads();
     // (B) sweeps: warp w sweeps slots w, w + kNutsWarps, ...
     if (gw) {
-      for (int slot = warp; slot < SLOTS; slot += kNutsWarps) {
+      for (int slot = sw; slot < SLOTS; slot += kNutsWarps) {
         MT* mw = mom[slot];
         for (int i = lane; i < NDET * kNMom * 2; i += 32) mw[i] = MT(0);
         __syncwarp();
@@ -561,20 +612,20 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(NutsArgs A) {
     }
     __syncthreads();
     // (C) epilogues and state machines
-    if (warp == 0 && lane < SLOTS && S.pending[lane]) {
+    if (warp == cw && lane < SLOTS && S.pending[lane]) {
       Nuts<PREC, NDET, SLOTS> nu(A, S, lane);
       double x[kMaxDim];
       for (int i = 0; i < D; ++i) x[i] = nu.X(P_N, i);
       if (gw) {
-        double gph[SHARPY_NPHYS];
+        DT gph[SHARPY_NPHYS];
         sl.lnl_new = NAN;
         if (sc[lane].ok) {
           epilogue<DT, true>(A.ev, sc[lane], ec[lane], mom[lane], &sl.lnl_new, gph);
           sl.st_bins += (double)(sc[lane].kisco + 1) * A.ev.n_det;
         }
-        for (int i = 0; i < D; ++i) gl_new[i] = sc[lane].ok ? (VT)gph[A.m.phys[i]] : (VT)NAN;
+        for (int i = 0; i < D; ++i) gl_new[i] = sc[lane].ok ? gph[A.m.phys[i]] : (VT)NAN;
       }
-      lp_new = nu.prior(x, glp_new);
+      lp_new = nu.template prior<false>(x, glp_new);
       if (!isfinite(sl.lnl_new)) sl.lnl_new = -INFINITY;  // rejected leaf (U = +inf)
       for (int i = 0; i < D; ++i)
         if (!isfinite(gl_new[i])) gl_new[i] = VT(0);
@@ -583,7 +634,7 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(NutsArgs A) {
     }
   }
   // write back
-  if (warp == 0 && lane < SLOTS && sl.pid < A.n) {
+  if (warp == cw && lane < SLOTS && sl.pid < A.n) {
     Nuts<PREC, NDET, SLOTS> nu(A, S, lane);
     for (int i = 0; i < D; ++i) {
       A.theta[sl.pid * D + i] = nu.X(P_P, i);
@@ -604,18 +655,21 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(NutsArgs A) {
 }
 
 // Launch helper for one (precision, detector count); the slot count is picked
-// by the caller. Defined in nuts_inst.cu, compiled once per combination.
-int launch_nuts(int precision, int ndet, int slots, const NutsArgs& A, cudaStream_t s);
+// by the caller; grid 0 means one CTA per SLOTS particles of A (a batched
+// launch passes its CTA count). Defined in nuts_inst.cu, compiled once per
+// combination.
+int launch_nuts(int precision, int ndet, int slots, const NutsArgs& A, unsigned grid, cudaStream_t s);
 
 template <int P, int ND>
-int launch_nuts_impl(int slots, const NutsArgs& A, cudaStream_t s) {
+int launch_nuts_impl(int slots, const NutsArgs& A, unsigned grid, cudaStream_t s) {
   auto go = [&](auto kernel, int sl, size_t bytes) -> int {
     if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
       return SHARPY_ECUDA;
-    dim3 grid((unsigned)((A.n + sl - 1) / sl));
-    kernel<<<grid, kNutsWarps * 32, bytes, s>>>(A);
+    const unsigned g = grid ? grid : (unsigned)((A.n + sl - 1) / sl);
+    kernel<<<g, kNutsWarps * 32, bytes, s>>>(A);
     return cudaGetLastError() == cudaSuccess ? SHARPY_OK : SHARPY_ECUDA;
   };
+  if (slots == 32) return go(nuts_kernel<P, ND, 32>, 32, sizeof(NutsSmem<P, ND, 32>));
   if (slots == 16) return go(nuts_kernel<P, ND, 16>, 16, sizeof(NutsSmem<P, ND, 16>));
   return go(nuts_kernel<P, ND, 8>, 8, sizeof(NutsSmem<P, ND, 8>));
 }

@@ -18,6 +18,8 @@
 // patterns, the amplitude, every Jacobian entry and the gradient contraction
 // are FP32 (relative error ~1e-7, far inside the 1e-4 gradient tolerance).
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace sharpy {
@@ -173,10 +175,50 @@ __device__ __forceinline__ void to_physical(const DevModel& m, const double* th,
   for (int i = 0; i < m.n_dim; ++i) ph[m.phys[i]] = th[i];
 }
 
+// u = (pi Tsun M)^(1/3) = (pi Tsun Mc)^(1/3) eta^(-1/5), 1/u and ln u for the
+// mixed path with one FP64 transcendental instead of three: u = c^(1/15) with
+// c = (pi Tsun Mc)^5 / eta^3. v = 1/u = c^(-1/15) from an FP32 start and two
+// division-free Newton steps v <- v + v (1 - c v^15) / 15 in FP64 (quadratic:
+// 1e-7 -> 1e-13 -> rounding), u = c v^14, ln u = log(u) in FP64 (it sets the
+// constant and 3PN phase terms, which need ~1e-10). Derivatives from
+// d ln u = (d Mc / Mc - 3/5 d eta / eta) / 3.
+__device__ __forceinline__ void u_mixed(double mc, const I4<float>& mcv, const I4<float>& eta, const I4<float>& ieta,
+                                        I4<float>& u, I4<float>& ui, I4<float>& lnu) {
+  const double p = (kPi * kTsun) * mc;
+  const double p2 = p * p;
+  const double ie = ieta.v;
+  const double c = (p2 * p2 * p) * (ie * ie * ie);
+  double v = (double)powf((float)c, -1.0f / 15.0f);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double v2 = v * v, v4 = v2 * v2, v8 = v4 * v4;
+    const double v15 = v8 * v4 * v2 * v;
+    v = fma(v * (1.0 / 15.0), fma(-c, v15, 1.0), v);
+  }
+  const double v2 = v * v, v4 = v2 * v2, v8 = v4 * v4;
+  const double uu = c * (v8 * v4 * v2);
+  const float uf = (float)uu;
+  const double l = log(uu);
+  const float vf = (float)v;
+  lnu.v = l;
+  lnu.vf = (float)l;
+  u.v = uu;
+  u.vf = uf;
+  ui.v = v;
+  ui.vf = vf;
+  const float imc = 1.0f / mcv.vf, ieta_f = 1.0f / eta.vf;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    lnu.d[i] = (1.0f / 3.0f) * (mcv.d[i] * imc - 0.6f * eta.d[i] * ieta_f);
+    u.d[i] = uf * lnu.d[i];
+    ui.d[i] = -vf * lnu.d[i];
+  }
+}
+
 // TaylorF2 phase coefficients in turns and their Jacobian w.r.t. (Mc, q, chi1, chi2).
-// Transcendentals in FP64: ln eta, ln Mc and one exponential (u).
+// FP64 path: ln eta, ln Mc and one exponential (u) in FP64; mixed path: u_mixed.
 template <class DT>
-__device__ void pn_coefficients(const double* ph, I4<DT>* alpha, I4<DT>& cpn, double& mtot) {
+__device__ void pn_coefficients(const double* ph, I4<DT>* alpha, I4<DT>& cpn, double& mtot, double& fisco) {
   const I4<DT> mc = ivar<DT>(ph[SHARPY_MC], 0);
   const I4<DT> q = ivar<DT>(ph[SHARPY_Q], 1);
   const I4<DT> c1 = ivar<DT>(ph[SHARPY_CHI1], 2);
@@ -186,10 +228,21 @@ __device__ void pn_coefficients(const double* ph, I4<DT>* alpha, I4<DT>& cpn, do
   const I4<DT> m2 = q * m1;        // m2 / M
   const I4<DT> eta = m1 * m2;
   const I4<DT> delta = m1 - m2;
+  const I4<DT> iq = recip(q);
+  const I4<DT> ieta = onepq * onepq * iq;  // 1 / eta = (1+q)^2 / q
   // ln u = (ln(pi Tsun) + ln Mc - 3/5 ln eta) / 3, v = u f^(1/3), M = u^3 / (pi Tsun)
-  const I4<DT> lnu = (1.0 / 3.0) * ((-11.076356701842613) + (ilog(mc) + (-0.6) * ilog(eta)));
-  const I4<DT> u = iexp(lnu);
-  mtot = u.v * u.v * u.v / (kPi * kTsun);
+  I4<DT> lnu, u, ui;
+  if constexpr (std::is_same<DT, double>::value) {
+    lnu = (1.0 / 3.0) * ((-11.076356701842613) + (ilog(mc) + (-0.6) * ilog(eta)));
+    u = iexp(lnu);
+    ui = recip(u);
+    mtot = u.v * u.v * u.v / (kPi * kTsun);
+    fisco = 1.0 / (14.696938456699069 * kPi * kTsun * mtot);  // 6^(3/2) pi M
+  } else {
+    u_mixed(ph[SHARPY_MC], mc, eta, ieta, u, ui, lnu);
+    mtot = u.v * u.v * u.v * (1.0 / (kPi * kTsun));
+    fisco = (ui.v * ui.v * ui.v) * (1.0 / 14.696938456699069);  // 1 / (6^(3/2) u^3)
+  }
   const I4<DT> chis = 0.5 * (c1 + c2);
   const I4<DT> chia = 0.5 * (c1 - c2);
   const I4<DT> eta2 = eta * eta;
@@ -209,9 +262,8 @@ __device__ void pn_coefficients(const double* ph, I4<DT>* alpha, I4<DT>& cpn, do
       ((-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * kPi * kPi) * eta + (76055.0 / 1728.0) * eta2 +
        (-127825.0 / 1296.0) * (eta2 * eta));
   const I4<DT> p7 = kPi * ((77096675.0 / 254016.0) + ((378515.0 / 1512.0) * eta + (-74045.0 / 756.0) * eta2));
-  // 3 / (128 eta) in turns; 1/eta = (1+q)^2 / q
-  const I4<DT> nt = (3.0 / (128.0 * kTwoPi)) * (onepq * onepq * recip(q));
-  const I4<DT> ui = recip(u);
+  // 3 / (128 eta) in turns
+  const I4<DT> nt = (3.0 / (128.0 * kTwoPi)) * ieta;
   const I4<DT> ui2 = ui * ui;
   const I4<DT> ui3 = ui2 * ui;
   alpha[0] = nt * (ui3 * ui2);  // x^5
@@ -247,10 +299,14 @@ __device__ __forceinline__ AT quad(const AT (*D)[3], const AT* a, const AT* b) {
 }
 
 __device__ __forceinline__ void sincos2psi(double psi, double* s2, double* c2) { sincos(2.0 * psi, s2, c2); }
+__device__ __forceinline__ const double* det_rc(const DevDetector& det, double*) { return det.rcd; }
+__device__ __forceinline__ const float* det_rc(const DevDetector& det, float*) { return det.rcf; }
 __device__ __forceinline__ void sincos2psi(double psi, float* s2, float* c2) { sincosf(2.0f * (float)psi, s2, c2); }
 __device__ __forceinline__ const double (*det_tensor(const DevDetector& det, double))[3] { return det.D; }
 __device__ __forceinline__ const float (*det_tensor(const DevDetector& det, float))[3] { return det.Df; }
 
+// Geocentric delay in FP64 (it multiplies frequencies up to kHz in the
+// phase); patterns and all derivatives in type AT.
 template <class AT>
 static __device__ void antenna(const DevDetector& det, double sa, double ca, double cd, double sdec, AT s2, AT c2,
                                Antenna<AT>& out) {
@@ -262,9 +318,9 @@ static __device__ void antenna(const DevDetector& det, double sa, double ca, dou
     out.ddt[0] = out.ddt[1] = AT(0);
     return;
   }
-  const double* r = det.r;
-  // geocentric delay in FP64 (it multiplies frequencies up to kHz in the phase)
-  out.dt = -(r[0] * (cd * ca) + r[1] * (cd * sa) + r[2] * sdec) * (1.0 / kClight);
+  const double* rd = det.rcd;  // position / c
+  out.dt = -(rd[0] * (cd * ca) + rd[1] * (cd * sa) + rd[2] * sdec);
+  const AT* rc = det_rc(det, (AT*)nullptr);
   const AT a_s = (AT)sa, a_c = (AT)ca, a_d = (AT)cd, a_z = (AT)sdec;
   const AT p[3] = {a_s, -a_c, AT(0)};
   const AT q[3] = {a_z * a_c, a_z * a_s, -a_d};
@@ -286,7 +342,6 @@ static __device__ void antenna(const DevDetector& det, double sa, double ca, dou
   out.dfc[1] = -s2 * dfp0_ra + c2 * dfc0_ra;
   out.dfp[2] = c2 * dfp0_sd + s2 * dfc0_sd;
   out.dfc[2] = -s2 * dfp0_sd + c2 * dfc0_sd;
-  const AT rc[3] = {(AT)(r[0] / kClight), (AT)(r[1] / kClight), (AT)(r[2] / kClight)};
   // d n / d ra = (-cd sa, cd ca, 0); d n / d sin dec = (-sdec ca / cd, -sdec sa / cd, 1)
   out.ddt[0] = -(rc[0] * (-a_d * a_s) + rc[1] * (a_d * a_c));
   out.ddt[1] = -(rc[0] * (-a_z * a_c / a_d) + rc[1] * (-a_z * a_s / a_d) + rc[2]);
@@ -295,7 +350,7 @@ static __device__ void antenna(const DevDetector& det, double sa, double ca, dou
 // Last bin with f_k <= f_isco, using the staged frequency table.
 __device__ __forceinline__ int isco_bin(const DevEvent& ev, double fisco) {
   int64_t K = ev.n_bins;
-  double t = floor((fisco - ev.f_min) / ev.df);
+  double t = floor((fisco - ev.f_min) * ev.inv_df);
   int64_t k = t < -1.0 ? -1 : (t > (double)(K - 1) ? K - 1 : (int64_t)t);
   while (k + 1 < K && ev.f[k + 1] <= fisco) ++k;
   while (k >= 0 && ev.f[k] > fisco) --k;
@@ -317,8 +372,8 @@ __device__ void prologue(const DevModel& m, const DevEvent& ev, const double* th
     return;
   }
   I4<DT> alpha[kNPn], cpn;
-  double mtot;
-  pn_coefficients<DT>(ph, alpha, cpn, mtot);
+  double mtot, fisco;
+  pn_coefficients<DT>(ph, alpha, cpn, mtot, fisco);
 #pragma unroll
   for (int j = 0; j < kNPn; ++j) {
     sc.alpha[j] = alpha[j].v;
@@ -330,7 +385,6 @@ __device__ void prologue(const DevModel& m, const DevEvent& ev, const double* th
   if (GRAD)
 #pragma unroll
     for (int i = 0; i < 4; ++i) ec.dc0[i] = cpn.d[i];
-  const double fisco = 1.0 / (14.696938456699069 * kPi * kTsun * mtot);  // 6^(3/2) pi M
   sc.kisco = isco_bin(ev, fisco);
 
   // Newtonian amplitude of an optimally oriented source: sqrt(5/24) pi^(-2/3) (T Mc)^(5/6) / D
@@ -342,18 +396,20 @@ __device__ void prologue(const DevModel& m, const DevEvent& ev, const double* th
     ec.rel_dl = DT(-1) / dl;
   }
   const DT ci = (DT)ph[SHARPY_COSI];
+  // sky position in FP64: the delays multiply frequencies up to kHz
   double sa = 0.0, ca = 1.0, cd = 1.0;
   DT s2 = DT(0), c2 = DT(1);
+  const double sdec = ph[SHARPY_SINDEC];
   bool any_sky = false;
   for (int a = 0; a < ev.n_det; ++a) any_sky = any_sky || !ev.det[a].fixed_response;
   if (any_sky) {
     sincos(ph[SHARPY_RA], &sa, &ca);
-    cd = sqrt(fmax(1.0 - ph[SHARPY_SINDEC] * ph[SHARPY_SINDEC], 0.0));
+    cd = sqrt(fmax(1.0 - sdec * sdec, 0.0));
     sincos2psi(ph[SHARPY_PSI], &s2, &c2);
   }
   for (int a = 0; a < ev.n_det; ++a) {
     Antenna<DT> an;
-    antenna<DT>(ev.det[a], sa, ca, cd, ph[SHARPY_SINDEC], s2, c2, an);
+    antenna<DT>(ev.det[a], sa, ca, cd, sdec, s2, c2, an);
     sc.tau[a] = ph[SHARPY_TC] + an.dt;
     const DT hp = DT(0.5) * (DT(1) + ci * ci);
     ec.cre[a] = an.fp * hp;
@@ -385,9 +441,9 @@ constexpr int kNMom = kNBasis + 1;
 // The gradient is contracted on the amplitude-scaled moments A0 Z, A0 Y_j and
 // the scaled prefix sum A0^2 P, which are O(SNR^2) and fit FP32 (the raw moments
 // and prefix sums span ~1e-22..1e43).
-template <class DT, bool GRAD, class MT>
+template <class DT, bool GRAD, class MT, class GT>
 __device__ void epilogue(const DevEvent& ev, const SweepCoef& sc, const EpiCoef<DT>& ec, const MT* mom, double* lnl,
-                         double* gph) {
+                         GT* gph) {
   double acc = -0.5 * ev.dd;
   DT g[SHARPY_NPHYS];
 #pragma unroll
@@ -437,7 +493,7 @@ __device__ void epilogue(const DevEvent& ev, const SweepCoef& sc, const EpiCoef<
   *lnl = acc;
   if (GRAD)
 #pragma unroll
-    for (int i = 0; i < SHARPY_NPHYS; ++i) gph[i] = (double)g[i];
+    for (int i = 0; i < SHARPY_NPHYS; ++i) gph[i] = (GT)g[i];
 }
 
 // Diagonal Gaussian mixture (test targets): ln L and its gradient.

@@ -3,6 +3,7 @@
 #include <cmath>
 
 #include "context.cuh"
+#include "tune.cuh"
 
 using namespace sharpy;
 
@@ -12,7 +13,8 @@ int enqueue_stage(sharpy_ctx* c, int64_t n, double* theta, double* lnl, double* 
                   int32_t* anc_out, double* cov, double* beta_state, cudaStream_t s);
 int enqueue_nuts(sharpy_ctx* c, int64_t n, const double* beta_ptr, double beta, double* theta, double* lnl,
                  double* grad, const double* inv_mass, const double* cov_step, double step, int max_depth,
-                 int n_steps, uint64_t key, uint32_t ctr, int precision, sharpy_nuts_stats* stats, cudaStream_t s);
+                 int n_steps, uint64_t key, uint32_t ctr, int precision, sharpy_nuts_stats* stats, cudaStream_t s,
+                 int slots);
 
 // Per-stage record: [beta, ess, dlnz, eps, accept_sum, depth_sum, n_leapfrog, n_divergent, active_bins]
 constexpr int kRec = 9;
@@ -68,8 +70,10 @@ extern "C" int sharpy_smc_run(sharpy_ctx* c, const sharpy_smc_options* o, uint64
   const int D = c->model.n_dim;
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
-  // run buffers: theta, grad [N][D], lnl [N], stats [N], scalars, cov, record
-  size_t bytes = (size_t)n * (2 * D + 1) * sizeof(double) + (size_t)n * sizeof(sharpy_nuts_stats) +
+  // run buffers: theta, grad [N][D], lnl [N], stats [N], scalars, cov, record;
+  // copies of theta, grad, lnl for the autotuner's trials when it has to run
+  const bool tune = !(c->tuned_slots && c->tuned_n == n && c->tuned_prec == o->precision);
+  size_t bytes = (size_t)n * (2 * D + 1) * sizeof(double) * (tune ? 2 : 1) + (size_t)n * sizeof(sharpy_nuts_stats) +
                  (8 + D * D + kRec) * sizeof(double);
   char* buf = nullptr;
   SHARPY_CUDA_TRY(cudaMallocAsync((void**)&buf, bytes, s));
@@ -84,6 +88,7 @@ extern "C" int sharpy_smc_run(sharpy_ctx* c, const sharpy_smc_options* o, uint64
   double* ess = sc + 3;
   double* cov = sc + 8;
   double* rec = cov + D * D;
+  double* trial = rec + kRec;  // [N][D] theta, [N][D] grad, [N] lnl (autotuner)
   int out = SHARPY_OK;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evr = nullptr;
   auto fail = [&](int code) {
@@ -112,9 +117,25 @@ extern "C" int sharpy_smc_run(sharpy_ctx* c, const sharpy_smc_options* o, uint64
     if (rc) return fail(rc);
     const double* minv = o->metric == 1 ? cov : nullptr;
     const double* cov_step = o->metric == 1 ? nullptr : cov;
+    if (t == 1 && tune) {
+      // pick the slot count on this stage: one transition on copies of the particles
+      auto go = [&](int slots, cudaStream_t ts) -> int {
+        SHARPY_CUDA_TRY(cudaMemcpyAsync(trial, th, (size_t)n * (2 * D + 1) * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, ts));
+        return enqueue_nuts(c, n, beta_state, 0.0, trial, trial + 2 * n * D, trial + n * D, minv, cov_step,
+                            o->eps_scale, o->max_depth, 1, key, (uint32_t)t << 8, o->precision, st, ts, slots);
+      };
+      TuneCandidate cands[kNumSlotChoices];
+      for (int i = 0; i < kNumSlotChoices; ++i) cands[i].slots = kSlotChoices[i];
+      int best = 0;
+      if ((rc = tune_slots(cands, kNumSlotChoices, go, s, &best))) return fail(rc);
+      c->tuned_slots = best;
+      c->tuned_n = n;
+      c->tuned_prec = o->precision;
+    }
     if (o->timing) cudaEventRecord(ev0, s);
     rc = enqueue_nuts(c, n, beta_state, 0.0, th, ll, gr, minv, cov_step, o->eps_scale, o->max_depth, o->n_mut, key,
-                      (uint32_t)t << 8, o->precision, st, s);
+                      (uint32_t)t << 8, o->precision, st, s, 0);
     if (rc) return fail(rc);
     if (o->timing) cudaEventRecord(ev1, s);
     stage_record_kernel<<<1, 1024, 0, s>>>(n, D, st, beta_next, ess, dlnz, cov, o->metric, o->eps_scale, rec);
