@@ -120,6 +120,13 @@ typedef struct {
   int max_stages;
   int timing;          /* 1: time each stage's NUTS launch with CUDA events (sharpy_stage.nuts_ms) */
   int pad;
+  /* Sample-recycling pool (sharpy_smc_run only; NULL: none): after the
+     mutation of stage t the N particles are copied to rows (t-1) N .. t N - 1
+     of pool_theta [pool_cap][D] and pool_lnl [pool_cap] (device), while they
+     fit (stages beyond pool_cap / N are not kept). */
+  double* pool_theta;
+  double* pool_lnl;
+  int64_t pool_cap;
 } sharpy_smc_options;
 
 typedef struct {
@@ -281,6 +288,23 @@ int sharpy_batch_stages(sharpy_batch* b, int e, sharpy_stage* stages, int cap, i
    use, picked by timing each candidate on the batch's own first stage (0
    before the first run). The results do not depend on it. */
 int sharpy_batch_slots(sharpy_batch* b);
+
+/* Sample recycling (Sec. 5, "Samples recycling"): a pool of m particles
+   collected after the mutation of every stage t = 1..T (particle of stage t
+   distributed as p_t = L^beta_t pi / Z_t), taken together as draws from the
+   mixture (1/T) sum_t p_t. Each gets its importance weight for the final
+   target p_T = L pi / Z_T:
+     ln w_i = ln L_i - ln Z_T - ln[(1/T) sum_t exp(beta_t ln L_i - ln Z_t)],
+   and a rejection step keeps particle i when u_i < w_i / max_j w_j, u_i the
+   first 53-bit uniform of Philox4x32-10 (key, counter (i mod 2^32,
+   i div 2^32, 7, 0)). theta [m][d], lnl [m]: device; beta [T], lnz_t [T]
+   (ln Z at each stage, i.e. the running sum of the stage increments): HOST;
+   log_w [m] device or NULL; out_theta [m][d] device or NULL: the kept
+   particles in pool order; *n_out (HOST) = number kept. Synchronous.
+   SHARPY_EINVAL on sizes out of range or non-finite beta / ln Z_t. */
+int sharpy_recycle(int64_t m, int d, int t, const double* theta, const double* lnl, const double* beta,
+                   const double* lnz_t, uint64_t key, double* log_w, double* out_theta, int64_t* n_out,
+                   sharpy_stream stream);
 
 /* Measurement helper: FP32 FMA TFLOP/s, FP64 FMA TFLOP/s and SFU sin+cos
    Gop/s of `device` from register-only kernels (out[3], host). Used as the

@@ -98,6 +98,8 @@ _SIGS = {
     "ref_waveform": (C.c_int, [_P(Model), _P(Event), _D, _D]),
     "ref_loglike": (C.c_int, [_P(Model), _P(Event), C.c_int64, _D, _D, _D]),
     "ref_set_threads": (C.c_int, [C.c_int]),
+    "ref_recycle_weights": (C.c_int, [C.c_int64, C.c_int, _D, _D, _D, _D]),
+    "ref_rejection_sample": (C.c_int, [C.c_int64, _D, C.c_uint64, _P(C.c_int32)]),
     "ref_prior_sample": (C.c_int, [_P(Model), C.c_int64, _D, C.c_uint64, C.c_uint32]),
     "ref_prior_logpdf_grad": (C.c_int, [_P(Model), C.c_int64, _D, _D, _D]),
     "ref_nuts_mutate": (C.c_int, [_P(Model), _P(Event), C.c_int64, C.c_double, _D, _D, _D, _D,
@@ -327,3 +329,23 @@ def smc_run(model, event, n_particles, alpha, n_mut, max_depth, metric, eps_scal
         raise RuntimeError(f"oracle smc_run did not reach beta = 1 (rc={rc})")
     rec = [dict((f, getattr(stages[i], f)) for f, _ in Stage._fields_) for i in range(ns.value)]
     return lnz.value, th, lnl, rec
+
+
+def recycle_weights(lnl, beta, lnz_t):
+    """ln w of pooled particles for the final target (Sec. 5, sample recycling)."""
+    lnl = _f64(lnl)
+    beta = _f64(beta)
+    lnz_t = _f64(lnz_t)
+    out = np.zeros(lnl.shape[0])
+    _check(lib().ref_recycle_weights(lnl.shape[0], beta.shape[0], _dp(lnl), _dp(beta), _dp(lnz_t), _dp(out)),
+           "recycle_weights")
+    return out
+
+
+def rejection_sample(log_w, key):
+    """0/1 keep flags of the rejection step of sample recycling."""
+    log_w = _f64(log_w)
+    keep = np.zeros(log_w.shape[0], dtype=np.int32)
+    _check(lib().ref_rejection_sample(log_w.shape[0], _dp(log_w), key,
+                                      keep.ctypes.data_as(C.POINTER(C.c_int32))), "rejection_sample")
+    return keep

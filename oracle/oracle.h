@@ -167,6 +167,19 @@ int ref_systematic_resample(int64_t n, const double* w, double u, int32_t* anc);
 /* Weighted mean-centred covariance [D][D]. */
 int ref_weighted_cov(int d, int64_t n, const double* theta, const double* w, double* cov);
 
+/* Sample recycling (Sec. 5, "Samples recycling"): a pool of m particles of
+   the stages t = 1..T, particle i drawn from p_t(i) = L^beta_t pi / Z_t, stands
+   for the mixture p~ = (1/T) sum_t p_t. Its importance weight for the target
+   p_T = L pi / Z_T (beta_T = 1) is
+     ln w_i = ln L_i - ln Z_T - ln[(1/T) sum_t exp(beta_t ln L_i - ln Z_t)].
+   beta[T], lnz_t[T] (ln Z_t = ln Z at beta_t). */
+int ref_recycle_weights(int64_t m, int t, const double* lnl, const double* beta, const double* lnz_t,
+                        double* log_w);
+/* Rejection step of the recycling: particle i is kept when
+   u_i < w_i / max_j w_j, u_i the first uniform of Philox4x32-10 (key,
+   counter (i mod 2^32, i div 2^32, 7, 0)). keep[m] = 0/1. */
+int ref_rejection_sample(int64_t m, const double* log_w, uint64_t key, int32_t* keep);
+
 /* Full SMC run from the prior to beta = 1. */
 int ref_smc_run(const ref_model* m, const ref_event* ev, const ref_smc_opts* o, uint64_t key,
                 double* lnz, int* n_stages, double* theta_out, double* lnl_out,

@@ -449,3 +449,33 @@ int ref_smc_run(const ref_model* m, const ref_event* ev, const ref_smc_opts* o, 
 }
 
 }  // extern "C"
+
+// Sample recycling (Sec. 5): mixture weights of the pooled particles for the
+// final target, then rejection sampling to i.i.d. draws.
+int ref_recycle_weights(int64_t m, int t, const double* lnl, const double* beta, const double* lnz_t,
+                        double* log_w) {
+  if (m < 0 || t < 1) return -1;
+  const double lnz_final = lnz_t[t - 1];
+  for (int64_t i = 0; i < m; ++i) {
+    // ln sum_t exp(beta_t ln L_i - ln Z_t), with its largest term factored out
+    double mx = -INFINITY;
+    for (int s = 0; s < t; ++s) mx = std::fmax(mx, beta[s] * lnl[i] - lnz_t[s]);
+    double acc = 0.0;
+    for (int s = 0; s < t; ++s) acc += std::exp(beta[s] * lnl[i] - lnz_t[s] - mx);
+    const double ln_mix = mx + std::log(acc) - std::log((double)t);
+    log_w[i] = lnl[i] - lnz_final - ln_mix;
+  }
+  return 0;
+}
+
+int ref_rejection_sample(int64_t m, const double* log_w, uint64_t key, int32_t* keep) {
+  if (m < 0) return -1;
+  double mx = -INFINITY;
+  for (int64_t i = 0; i < m; ++i) mx = std::fmax(mx, log_w[i]);
+  for (int64_t i = 0; i < m; ++i) {
+    double u[2];
+    ref_uniform2(key, (uint32_t)i, (uint32_t)((uint64_t)i >> 32), 7u, 0u, u);
+    keep[i] = (u[0] < std::exp(log_w[i] - mx)) ? 1 : 0;
+  }
+  return 0;
+}

@@ -42,7 +42,8 @@ class SmcOptions(C.Structure):
     _fields_ = [("n_particles", C.c_int64), ("alpha", C.c_double), ("n_mut", C.c_int),
                 ("max_depth", C.c_int), ("metric", C.c_int), ("eps_scale", C.c_double),
                 ("precision", C.c_int), ("max_stages", C.c_int), ("timing", C.c_int),
-                ("pad", C.c_int)]
+                ("pad", C.c_int), ("pool_theta", C.c_void_p), ("pool_lnl", C.c_void_p),
+                ("pool_cap", C.c_int64)]
 
 
 class Stage(C.Structure):
@@ -88,6 +89,8 @@ _SIGS = {
     "sharpy_batch_particles": (C.c_int, [_VP, C.c_int, _VP, _VP, _VP]),
     "sharpy_batch_stages": (C.c_int, [_VP, C.c_int, C.POINTER(Stage), C.c_int, C.POINTER(C.c_int)]),
     "sharpy_batch_slots": (C.c_int, [_VP]),
+    "sharpy_recycle": (C.c_int, [C.c_int64, C.c_int, C.c_int, _VP, _VP, C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double), C.c_uint64, _VP, _VP, C.POINTER(C.c_int64), _VP]),
     "sharpy_get_status": (C.c_int, [_CTX]),
     "sharpy_clear_status": (C.c_int, [_CTX]),
     "sharpy_error_string": (C.c_char_p, [C.c_int]),

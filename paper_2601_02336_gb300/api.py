@@ -182,11 +182,20 @@ class Context:
         return lnz.value, ns.value
 
     def smc_run(self, n_particles, alpha, n_mut, max_depth, metric, eps_scale, key,
-                precision="mixed", max_stages=500, timing=False):
+                precision="mixed", max_stages=500, timing=False, pool_stages=0):
+        """Full SMC run. pool_stages > 0 also returns the sample-recycling pool:
+        (lnz, theta, lnl, records, pool_theta, pool_lnl) with the particles after
+        each of the first pool_stages stages."""
         o = SmcOptions(n_particles, alpha, n_mut, max_depth, metric, eps_scale, _prec(precision), max_stages,
                        1 if timing else 0, 0)
-        th = torch.empty((n_particles, self.n_dim), dtype=torch.float64, device=f"cuda:{self.device}")
-        ll = torch.empty(n_particles, dtype=torch.float64, device=th.device)
+        dev = f"cuda:{self.device}"
+        th = torch.empty((n_particles, self.n_dim), dtype=torch.float64, device=dev)
+        ll = torch.empty(n_particles, dtype=torch.float64, device=dev)
+        if pool_stages > 0:
+            cap = pool_stages * n_particles
+            pth = torch.empty((cap, self.n_dim), dtype=torch.float64, device=dev)
+            pll = torch.empty(cap, dtype=torch.float64, device=dev)
+            o.pool_theta, o.pool_lnl, o.pool_cap = pth.data_ptr(), pll.data_ptr(), cap
         stages = (Stage * max_stages)()
         lnz = C.c_double()
         ns = C.c_int()
@@ -194,6 +203,9 @@ class Context:
                                    stages, _stream()), "sharpy_smc_run")
         rec = [dict((f, getattr(stages[i], f)) for f, _ in Stage._fields_ if f != "pad")
                for i in range(ns.value)]
+        if pool_stages > 0:
+            rows = min(len(rec), pool_stages) * n_particles
+            return lnz.value, th, ll, rec, pth[:rows], pll[:rows]
         return lnz.value, th, ll, rec
 
     def status(self):
@@ -262,6 +274,33 @@ class Batch:
     @property
     def slots(self):
         return lib().sharpy_batch_slots(self._h)
+
+
+def recycle(theta, lnl, betas, lnz_t, key):
+    """Sample recycling (sharpy_recycle): importance weights of a pool drawn from
+    the stages' mixture, and the i.i.d. draws the rejection step keeps.
+    theta [m][d], lnl [m] device; betas, lnz_t: one entry per pooled stage.
+    Returns (log_w [m], kept theta [n_kept][d])."""
+    theta = _dev(theta, "theta")
+    lnl = _dev(lnl, "lnl")
+    m, d = theta.shape
+    t = len(betas)
+    b = (C.c_double * t)(*[float(x) for x in betas])
+    z = (C.c_double * t)(*[float(x) for x in lnz_t])
+    lw = torch.empty(m, dtype=torch.float64, device=theta.device)
+    out = torch.empty_like(theta)
+    n = C.c_int64()
+    check(lib().sharpy_recycle(m, d, t, _ptr(theta), _ptr(lnl), b, z, key, _ptr(lw), _ptr(out), C.byref(n),
+                               _stream()), "sharpy_recycle")
+    return lw, out[:n.value]
+
+
+def recycle_run(pool_theta, pool_lnl, records, n_particles, key):
+    """Recycle the pool of an smc_run(..., pool_stages=T): its stages' beta and running ln Z."""
+    t = pool_theta.shape[0] // n_particles
+    betas = [r["beta"] for r in records[:t]]
+    lnz_t = np.cumsum([r["dlnz"] for r in records[:t]])
+    return recycle(pool_theta, pool_lnl, betas, lnz_t, key)
 
 
 def systematic_resample(w, u):

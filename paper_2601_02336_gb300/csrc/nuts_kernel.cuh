@@ -97,6 +97,9 @@ struct NutsShared {
   int metric_kind;
   int alive;
   int pending[SLOTS];
+  int order[SLOTS];  // this tick's sweeps, longest (largest k_ISCO) first
+  int n_order;
+  int next;          // next entry of order to claim
 };
 
 // Elementary functions in the state machine's precision.
@@ -489,7 +492,6 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(const __grid_c
   // control warp: warp 0 or 2 by CTA parity, so the serial (FP64-heavy) phases
   // of two CTAs sharing an SM run on different SM sub-partitions
   const int cw = (blockIdx.x & 1) << 1;
-  const int sw = (warp - cw) & (kNutsWarps - 1);  // this warp's rank in the sweep order
   const int D = A.m.n_dim;
   const bool gw = A.m.model == SHARPY_MODEL_TAYLORF2;
 
@@ -600,14 +602,34 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(const __grid_c
         for (int i = 0; i < D; ++i) gl_new[i] = (VT)g[i];
       }
     }
+    if (gw && warp == cw) {
+      // order this tick's sweeps by decreasing k_ISCO (ties: slot order)
+      const int key = (lane < SLOTS && S.pending[lane] && sc[lane].ok) ? sc[lane].kisco : -2;
+      int rank = 0;
+#pragma unroll
+      for (int j = 0; j < SLOTS; ++j) {
+        const int kj = __shfl_sync(0xffffffffu, key, j);
+        rank += (kj > key || (kj == key && j < lane)) ? 1 : 0;
+      }
+      if (key >= -1) S.order[rank] = lane;
+      const unsigned sweeps = __ballot_sync(0xffffffffu, key >= -1);
+      if (lane == 0) {
+        S.n_order = __popc(sweeps);
+        S.next = 0;
+      }
+    }
     __syncthreads();
-    // (B) sweeps: warp w sweeps slots w, w + kNutsWarps, ...
+    // (B) sweeps: each warp claims the next sweep of the longest-first order
+    // (a sweep writes all its moments; the warp that runs it does not change
+    // the result)
     if (gw) {
-      for (int slot = sw; slot < SLOTS; slot += kNutsWarps) {
-        MT* mw = mom[slot];
-        for (int i = lane; i < NDET * kNMom * 2; i += 32) mw[i] = MT(0);
-        __syncwarp();
-        if (S.pending[slot] && sc[slot].ok) sweep<PREC, true, NDET>(A.ev, sc[slot], mw);
+      for (;;) {
+        int k = 0;
+        if (lane == 0) k = atomicAdd(&S.next, 1);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= S.n_order) break;
+        const int slot = S.order[k];
+        sweep<PREC, true, NDET>(A.ev, sc[slot], mom[slot]);
       }
     }
     __syncthreads();

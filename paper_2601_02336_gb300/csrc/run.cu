@@ -138,6 +138,13 @@ extern "C" int sharpy_smc_run(sharpy_ctx* c, const sharpy_smc_options* o, uint64
                       (uint32_t)t << 8, o->precision, st, s, 0);
     if (rc) return fail(rc);
     if (o->timing) cudaEventRecord(ev1, s);
+    if (o->pool_theta && o->pool_lnl && (int64_t)t * n <= o->pool_cap) {
+      const int64_t row = (int64_t)(t - 1) * n;
+      if (cudaMemcpyAsync(o->pool_theta + row * D, th, n * D * sizeof(double), cudaMemcpyDeviceToDevice, s) !=
+              cudaSuccess ||
+          cudaMemcpyAsync(o->pool_lnl + row, ll, n * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return fail(SHARPY_ECUDA);
+    }
     stage_record_kernel<<<1, 1024, 0, s>>>(n, D, st, beta_next, ess, dlnz, cov, o->metric, o->eps_scale, rec);
     if (cudaGetLastError() != cudaSuccess) return fail(SHARPY_ECUDA);
     if (cudaMemcpyAsync(c->h_pinned, rec, kRec * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -24,6 +24,7 @@ constexpr int kSmcThreads = 1024;  // single-CTA prefix kernel of the plain resa
 constexpr int kRwWarps = kRwThreads / 32;
 constexpr int kGrid = 54;          // FP32 grid db_m = hi 2^-m
 constexpr int kGridChunk = 9;      // grid points per pass
+constexpr int kNewton32 = 8;       // FP32 Newton passes at most
 constexpr int kCovThreads = 256;
 
 struct RwShared {
@@ -206,10 +207,12 @@ __global__ void __cluster_dims__(kRwCluster, 1, 1) __launch_bounds__(kRwThreads)
       while (m < kGrid - 1 && 2.0f * logf(sh.s1grid[m + 1]) - logf(sh.s1grid[m]) < ltf) ++m;
       const double glo = (m < kGrid - 1) ? ldexp(hi, -m) : 0.0;
       const double gup = ldexp(hi, 1 - m);
-      // FP32 Newton inside the bracket
+      // FP32 Newton inside the bracket, on t = ln db (g is smooth in t across
+      // the decades db spans); FP32 sums carry ~1e-6 relative noise, so a few
+      // steps to ~1e-5 are all FP32 can give: the FP64 steps below finish
       float flo = (float)glo, fup = (float)gup;
       float x = glo > 0.0 ? sqrtf(flo * fup) : 0.5f * fup;
-      for (int it = 0; it < 30; ++it) {
+      for (int it = 0; it < kNewton32; ++it) {
         float sf[4];
         sums32(xf, n, i0, step, x, sf, sh);
         const float g = 2.0f * logf(sf[0]) - logf(sf[1]) - ltf;
@@ -217,19 +220,20 @@ __global__ void __cluster_dims__(kRwCluster, 1, 1) __launch_bounds__(kRwThreads)
           flo = x;
         else
           fup = x;
-        const float gp = 2.0f * (sf[2] / sf[0] - sf[3] / sf[1]);
-        float xn = x - g / gp;
-        if (!(xn > flo && xn < fup)) xn = 0.5f * (flo + fup);
-        const bool done = fabsf(xn - x) <= 1e-6f * x || !(fup - flo > 1e-6f * fup);
+        const float gt = 2.0f * (sf[2] / sf[0] - sf[3] / sf[1]) * x;  // dg / d ln db
+        float xn = x * expf(-g / gt);
+        if (!(xn > flo && xn < fup)) xn = flo > 0.0f ? sqrtf(flo * fup) : 0.5f * fup;
+        const bool done = fabsf(xn - x) <= 1e-5f * x || !(fup - flo > 1e-5f * fup);
         x = xn;
         if (done) break;
       }
-      // FP64 Newton from the FP32 root, bracketed by [lo, up] (g(0) >= 0 > g(hi));
-      // once it has converged, evaluate just below the root to verify a point
+      // FP64 Newton from the FP32 root, bracketed by [lo, up] (g(0) >= 0 > g(hi)).
+      // Converged (Newton step within 2e-12, or g at its rounding noise): a point
+      // with g >= 0 is the answer; from above, step 1e-12 below the root's
+      // estimate and evaluate there. Typically 2-3 passes.
       double lo = 0.0, up = hi;
       double xd = (double)x;
       if (!(xd > 0.0 && xd < hi)) xd = glo > 0.0 ? sqrt(glo * gup) : 0.5 * gup;
-      bool verify = false;
       for (int it = 0; it < 60; ++it) {
         double sd[4];
         sums64(A.lnl, n, i0, step, mx, xd, sd, sh);
@@ -238,11 +242,11 @@ __global__ void __cluster_dims__(kRwCluster, 1, 1) __launch_bounds__(kRwThreads)
           lo = fmax(lo, xd);
         else
           up = fmin(up, xd);
-        if (verify && g >= 0.0) break;
         const double gp = 2.0 * (sd[2] / sd[0] - sd[3] / sd[1]);
-        double xn = xd - g / gp;
-        verify = fabs(xn - xd) <= 1e-12 * xd;
-        if (verify) xn *= 1.0 - 1e-12;
+        const double xr = xd - g / gp;  // Newton's estimate of the root
+        const bool conv = fabs(xr - xd) <= 2e-12 * xd || fabs(g) <= 1e-13;
+        if (conv && g >= 0.0) break;
+        double xn = conv ? xr * (1.0 - 1e-12) : xr;
         if (!(xn > lo && xn < up)) xn = lo > 0.0 ? 0.5 * (lo + up) : 0.5 * fmin(xd, up);
         if (!(up - lo > 1e-12 * up)) break;
         xd = xn;

@@ -39,23 +39,72 @@ __device__ __forceinline__ int acc_to_mom(int i) {
   return mom_index(i / 2, 9, i & 1);
 }
 
+// Warp reduce-scatter of NP per-lane values (NP a power of two): at each
+// butterfly level a lane keeps one half of its values and sends the other
+// half to its partner, so the 32-lane sums of all NP values take
+// NP/2 + NP/4 + ... shuffles instead of 5 NP. Fixed pairing: deterministic.
+// Afterwards, for NP >= 32, lane l holds the sums of values
+// l (NP/32) ... l (NP/32) + NP/32 - 1 in v[0 .. NP/32); for NP < 32 the lanes
+// of each group of 32/NP consecutive lanes all hold the sum of value
+// l / (32/NP) in v[0].
+template <int N, int OFF>
+struct ReduceScatter {
+  static __device__ __forceinline__ void run(float* v, int lane) {
+    constexpr int H = N / 2;
+    const bool up = (lane & OFF) != 0;
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      const float send = up ? v[j] : v[j + H];
+      const float keep = up ? v[j + H] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, OFF);
+    }
+    ReduceScatter<H, OFF / 2>::run(v, lane);
+  }
+};
+template <int OFF>
+struct ReduceScatter<1, OFF> {
+  static __device__ __forceinline__ void run(float* v, int) {
+#pragma unroll
+    for (int o = OFF; o >= 1; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+  }
+};
+template <int N>
+struct ReduceScatter<N, 0> {
+  static __device__ __forceinline__ void run(float*, int) {}
+};
+template <>
+struct ReduceScatter<1, 0> {
+  static __device__ __forceinline__ void run(float*, int) {}
+};
+
+template <int NACC>
+struct FlushShape {
+  static constexpr int NP = NACC <= 2 ? 2 : NACC <= 4 ? 4 : NACC <= 8 ? 8 : NACC <= 16 ? 16 : NACC <= 32 ? 32 : 64;
+  static constexpr int KEEP = NP >= 32 ? NP / 32 : 1;  // sums held per lane
+  static __device__ __forceinline__ int index(int lane, int t) { return NP >= 32 ? lane * KEEP + t : lane / (32 / NP); }
+  static __device__ __forceinline__ bool owner(int lane) { return NP >= 32 || lane % (32 / NP) == 0; }
+};
+
 // Flush per-lane FP32 partials into the lane-distributed outer accumulators:
-// each block sum (fixed-order warp tree) is added with an error-free two-sum,
+// each block sum (reduce-scatter above) is added with an error-free two-sum,
 // so the outer sums carry ~48 bits without FP64 arithmetic.
 template <int NACC>
 __device__ __forceinline__ void flush(float* acc, float* hi, float* lo, int lane) {
+  using F = FlushShape<NACC>;
+  static_assert(NACC <= 64, "at most 64 moments per lane");
+  float v[F::NP];
 #pragma unroll
-  for (int i = 0; i < NACC; ++i) {
-    float v = warp_sum(acc[i]);
-    if ((i & 31) == lane) {
-      const int o = i >> 5;
-      const float s = hi[o] + v;
-      const float bp = s - hi[o];
-      lo[o] += (hi[o] - (s - bp)) + (v - bp);
-      hi[o] = s;
-    }
-    acc[i] = 0.0f;
+  for (int i = 0; i < F::NP; ++i) v[i] = i < NACC ? acc[i] : 0.0f;
+  ReduceScatter<F::NP, 16>::run(v, lane);
+#pragma unroll
+  for (int t = 0; t < F::KEEP; ++t) {
+    const float s = hi[t] + v[t];
+    const float bp = s - hi[t];
+    lo[t] += (hi[t] - (s - bp)) + (v[t] - bp);
+    hi[t] = s;
   }
+#pragma unroll
+  for (int i = 0; i < NACC; ++i) acc[i] = 0.0f;
 }
 
 // Magic constant for exact round-to-nearest of |x| < 2^22 in FP32.
@@ -69,7 +118,7 @@ __device__ __forceinline__ float frac_turn(float x) {
 template <bool GRAD, int NDET, bool SPLIT>
 __device__ void sweep_mixed(const DevEvent& ev, const SweepCoef& sc, float* mom) {
   constexpr int NACC = MomCount<NDET, GRAD>::value;
-  constexpr int NOUT = (NACC + 31) / 32;
+  constexpr int NOUT = FlushShape<NACC>::KEEP;
   const int lane = threadIdx.x & 31;
   const int64_t K = ev.n_bins;
   float acc[NACC];
@@ -172,10 +221,12 @@ __device__ void sweep_mixed(const DevEvent& ev, const SweepCoef& sc, float* mom)
   }
   // Every lane takes part in the final flush (warp-uniform).
   flush<NACC>(acc, hi, lo, lane);
+  if (FlushShape<NACC>::owner(lane)) {
 #pragma unroll
-  for (int i = 0; i < NOUT; ++i) {
-    int idx = i * 32 + lane;
-    if (idx < NACC) mom[acc_to_mom<NDET, GRAD>(idx)] = hi[i] + lo[i];
+    for (int t = 0; t < NOUT; ++t) {
+      const int idx = FlushShape<NACC>::index(lane, t);
+      if (idx < NACC) mom[acc_to_mom<NDET, GRAD>(idx)] = hi[t] + lo[t];
+    }
   }
 }
 

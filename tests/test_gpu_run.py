@@ -85,3 +85,25 @@ def test_run_mixed_lnz_within_two_se(precision):
                        precision=precision)[0] for s in range(R)]
     assert abs(np.mean(got) - np.mean(ref)) <= 2.0 * math.sqrt(_se(got) ** 2 + _se(ref) ** 2), (got, ref)
     assert ctx.status() == 0
+
+
+def test_run_bimodal11_analytic_evidence():
+    """The bimodal 11-D target of App. A (two normalised Gaussians, sigma^2 = 0.01; alpha 0.95 as in the
+    paper): ln Z = ln 2 - 11 ln 10 with the [-5, 5]^11 box prior, on both NUTS state-machine precisions;
+    both modes keep their mass."""
+    G.require_gpu()
+    w = inputs.bimodal11(n_particles=4096)
+    ctx = api.Context(api.gaussmix_config(w.lo, w.hi, w.logw, w.mu, w.sigma))
+    truth = math.log(2.0) - 11 * math.log(10.0)
+    for prec in ("fp64", "mixed"):
+        lnzs, fracs = [], []
+        for s in range(6):
+            lnz, th, lnl, rec = ctx.smc_run(w.n_particles, w.alpha, w.n_mut, w.max_depth, w.metric, w.eps_scale,
+                                            key=1300 + s, precision=prec)
+            lnzs.append(lnz)
+            fracs.append(float((th[:, 0] > 0).double().mean()))
+        # the share of a mode is frozen once the modes separate and varies from run to run; no mode is
+        # lost and, over the runs, neither is favoured
+        assert min(fracs) > 0.05 and max(fracs) < 0.95, (prec, fracs)
+        assert abs(np.mean(fracs) - 0.5) < 0.2, (prec, fracs)
+        assert abs(np.mean(lnzs) - truth) < 4 * _se(lnzs) + 0.1, (prec, lnzs, truth)
