@@ -47,6 +47,25 @@ WORK = {
 }
 
 
+# DRAM bytes (read + write) of one NUTS launch of this workload from an ncu
+# capture (profiles/nuts_kernel_bbh11.md), valid only for the kernel sources
+# it was taken on: reported as roofline.traffic while their hash matches.
+TRAFFIC_SOURCES = ["nuts_kernel.cuh", "sweep.cuh", "physics.cuh", "common.cuh"]
+TRAFFIC = {"sources_sha256_16": "3d6e6d91dcf306d1",
+           "mixed": 1736192 + 1003264, "split": 1793536 + 1057280}
+
+
+def _traffic(precision):
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2601_02336_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != TRAFFIC["sources_sha256_16"]:
+        return None
+    return TRAFFIC.get(precision)
+
+
 def _env_int(k, d):
     try:
         return int(os.environ.get(k, d))
@@ -410,7 +429,8 @@ def main():
     fp32_ach = bins * wk["fp32_flop"] / secs / 1e12
     kname = {"mixed": "MIXED", "split": "MIXED_SPLIT", "fp64": "FP64"}[args.precision]
     roofline = {"bound": "alu", "kernel": f"nuts_kernel<{kname},3>", "achieved": ach, "peak": peak,
-                "unit": "TFLOP/s", "frac": ach / peak if peak else None, "traffic": None,
+                "unit": "TFLOP/s", "frac": ach / peak if peak else None, "traffic": _traffic(args.precision),
+                "traffic_unit": "bytes per NUTS launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "pipe": wk["pipe"], "flop_per_active_bin_det": wk["flop"],
                 "peak_source": f"measured {wk['pipe'].upper()} FMA probe on this GPU (sharpy_probe_peaks)",
                 "fp32_achieved": fp32_ach, "fp32_peak": fp32_peak,
