@@ -98,6 +98,8 @@ _SIGS = {
     "ref_waveform": (C.c_int, [_P(Model), _P(Event), _D, _D]),
     "ref_loglike": (C.c_int, [_P(Model), _P(Event), C.c_int64, _D, _D, _D]),
     "ref_set_threads": (C.c_int, [C.c_int]),
+    "ref_fisher": (C.c_int, [_P(Model), _P(Event), C.c_int64, _D, _D]),
+    "ref_local_metric": (C.c_int, [_P(Model), _P(Event), C.c_int64, _D, C.c_double, _D]),
     "ref_recycle_weights": (C.c_int, [C.c_int64, C.c_int, _D, _D, _D, _D]),
     "ref_rejection_sample": (C.c_int, [C.c_int64, _D, C.c_uint64, _P(C.c_int32)]),
     "ref_prior_sample": (C.c_int, [_P(Model), C.c_int64, _D, C.c_uint64, C.c_uint32]),
@@ -349,3 +351,22 @@ def rejection_sample(log_w, key):
     _check(lib().ref_rejection_sample(log_w.shape[0], _dp(log_w), key,
                                       keep.ctypes.data_as(C.POINTER(C.c_int32))), "rejection_sample")
     return keep
+
+
+def fisher(model, event, theta):
+    """Fisher information <d_j h | d_k h> at each parameter vector: [N][D][D]."""
+    theta = _f64(np.atleast_2d(theta))
+    n, d = theta.shape
+    out = np.zeros((n, d, d))
+    _check(lib().ref_fisher(C.byref(model), C.byref(event.ev), n, _dp(theta), _dp(out)), "fisher")
+    return out
+
+
+def local_metric(model, event, theta, beta):
+    """Per-particle mass matrix beta F + prior Hessian + box precision: [N][D][D]."""
+    theta = _f64(np.atleast_2d(theta))
+    n, d = theta.shape
+    out = np.zeros((n, d, d))
+    evp = C.byref(event.ev) if event is not None else None
+    _check(lib().ref_local_metric(C.byref(model), evp, n, _dp(theta), beta, _dp(out)), "local_metric")
+    return out

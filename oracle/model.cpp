@@ -369,6 +369,86 @@ int ref_waveform(const ref_model* m, const ref_event* ev, const double* theta, d
   return 0;
 }
 
+// Fisher information: F_jk = sum_a sum_k w_k Re(conj(dh_j) dh_k), w = 4 df / S,
+// with dh the exact derivatives of the strain (dual numbers in every free
+// dimension).
+static void fisher_one(const ref_model* m, const ref_event* ev, const double* theta, double* F) {
+  using T = DualN<REF_MAX_DIM>;
+  const int D = m->n_dim;
+  T x[REF_MAX_DIM];
+  for (int i = 0; i < D; ++i) x[i] = T::variable(theta[i], i);
+  T ph[REF_NPHYS];
+  physical(m, x, ph);
+  T fisco = f_isco_t(ph[REF_MC], ph[REF_Q]);
+  for (int i = 0; i < D * D; ++i) F[i] = 0.0;
+  for (int a = 0; a < ev->n_det; ++a) {
+    Projection<T> pr;
+    antenna_t(&ev->det[a], ph[REF_RA], ph[REF_SINDEC], ph[REF_PSI], &pr.fp, &pr.fc, &pr.dt);
+    for (int64_t k = 0; k < ev->n_bins; ++k) {
+      double f = ev->f_min + (double)k * ev->df;
+      double w = 4.0 * ev->df / ev->psd[a * ev->n_bins + k];
+      T hre(0.0), him(0.0);
+      if (!strain_bin(ph, pr, fisco, f, &hre, &him)) continue;
+      for (int j = 0; j < D; ++j)
+        for (int l = 0; l < D; ++l) F[j * D + l] += w * (hre.d[j] * hre.d[l] + him.d[j] * him.d[l]);
+    }
+  }
+}
+
+int ref_fisher(const ref_model* m, const ref_event* ev, int64_t n, const double* theta, double* fisher) {
+  if (m->kind != REF_KIND_GW || !ev) return -1;
+  const int D = m->n_dim;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t i = 0; i < n; ++i) fisher_one(m, ev, theta + i * D, fisher + i * D * D);
+  return 0;
+}
+
+int ref_local_metric(const ref_model* m, const ref_event* ev, int64_t n, const double* theta, double beta,
+                     double* mass) {
+  const int D = m->n_dim;
+  if (m->kind == REF_KIND_GW) {
+    int rc = ref_fisher(m, ev, n, theta, mass);
+    if (rc) return rc;
+  } else {
+    // Gaussian mixture: the components' precisions weighted by their
+    // responsibilities at the point (the exact Hessian for one component)
+    for (int64_t i = 0; i < n; ++i) {
+      const double* x = theta + i * D;
+      double* M = mass + i * D * D;
+      for (int j = 0; j < D * D; ++j) M[j] = 0.0;
+      double lc[REF_MAX_COMP], best = -INFINITY;
+      for (int c = 0; c < m->n_comp; ++c) {
+        double t = m->mix_logw[c];
+        for (int j = 0; j < D; ++j) {
+          const double z = (x[j] - m->mix_mu[c][j]) / m->mix_sigma[c][j];
+          t += -0.5 * z * z - std::log(m->mix_sigma[c][j]);
+        }
+        lc[c] = t;
+        best = std::fmax(best, t);
+      }
+      double tot = 0.0;
+      for (int c = 0; c < m->n_comp; ++c) tot += std::exp(lc[c] - best);
+      for (int c = 0; c < m->n_comp; ++c) {
+        const double r = std::exp(lc[c] - best) / tot;
+        for (int j = 0; j < D; ++j) M[j * D + j] += r / (m->mix_sigma[c][j] * m->mix_sigma[c][j]);
+      }
+    }
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    double* M = mass + i * D * D;
+    for (int j = 0; j < D * D; ++j) M[j] *= beta;
+    for (int j = 0; j < D; ++j) {
+      const double w = m->hi[j] - m->lo[j];
+      M[j * D + j] += 12.0 / (w * w);
+      if (m->prior[j] == REF_PRIOR_POWER2) {
+        const double xj = theta[i * D + j];
+        M[j * D + j] += 2.0 / (xj * xj);
+      }
+    }
+  }
+  return 0;
+}
+
 int ref_set_threads(int n) {
 #ifdef _OPENMP
   const int prev = omp_get_max_threads();

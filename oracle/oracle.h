@@ -139,6 +139,24 @@ double ref_f_isco(double mc, double q);
 /* Detector-frame strain h_a(f_k) of one parameter vector theta (free dims). */
 int ref_waveform(const ref_model* m, const ref_event* ev, const double* theta, double* h);
 
+/* Fisher information of the Whittle likelihood (Sec. 2, Eq. 2) at N parameter
+   vectors: F_jk = <d_j h | d_k h> = sum_a sum_bins (4 df / S) Re(conj(d_j h) d_k h),
+   the derivatives of the strain taken exactly (dual numbers), h = 0 above
+   f_ISCO. F: [N][D][D]. (The Gauss-Newton part of -d^2 ln L: the part that
+   stays positive semi-definite.) TaylorF2 models only. */
+int ref_fisher(const ref_model* m, const ref_event* ev, int64_t n, const double* theta, double* fisher);
+
+/* Per-particle mass matrix of Sec. 5 ("Exploitation of local geometry"): the
+   Hessian of -ln[L^beta pi] at the particle, with the likelihood part replaced
+   by its Gauss-Newton part beta F (positive semi-definite), the prior part
+   exact (2 / d^2 for a prior proportional to d^2, 0 for uniform), plus the
+   precision 12 / width^2 of each uniform box so that the matrix stays positive
+   definite where F is degenerate (beta -> 0). For a Gaussian-mixture model F
+   is the components' precisions weighted by their responsibilities at the
+   point (the exact Hessian of -ln L for a single component). M: [N][D][D]. */
+int ref_local_metric(const ref_model* m, const ref_event* ev, int64_t n, const double* theta, double beta,
+                     double* mass);
+
 /* Number of OpenMP threads the particle loops use (timing only: every result
    is independent of it). Returns the previous setting. */
 int ref_set_threads(int n);
