@@ -289,6 +289,23 @@ int sharpy_batch_stages(sharpy_batch* b, int e, sharpy_stage* stages, int cap, i
    before the first run). The results do not depend on it. */
 int sharpy_batch_slots(sharpy_batch* b);
 
+/* Per-particle mass matrices (Sec. 5, "Exploitation of local geometry": at the
+   start of each SMC iteration every particle gets the Hessian of the tempered
+   posterior as its metric, fixed through the mutation). Reading: the
+   likelihood part is its Gauss-Newton part beta F(theta), F_jk = <d_j h|d_k h>
+   the Fisher information of Eq. (2) (positive semi-definite; the residual
+   term of the exact Hessian is dropped), plus the exact prior Hessian
+   (2 / d^2 for a prior proportional to d^2) and 12 / width^2 on the diagonal
+   (the precision of each uniform box) so that the matrix stays positive
+   definite where F is degenerate. Gaussian-mixture models: F = the
+   components' precisions weighted by their responsibilities. theta [N][D]
+   device; outputs (device, [N][D][D], each may be NULL but not all):
+   mass = M, inv_mass = M^-1, chol = L lower triangular with L L^T = M^-1.
+   The first call on a TaylorF2 context builds the prefix tables of
+   w f^-7/3 B_m B_n it needs (synchronous then; 54 x n_det x n_bins doubles). */
+int sharpy_local_metric(sharpy_ctx* ctx, int64_t n, const double* theta, double beta, double* mass,
+                        double* inv_mass, double* chol, sharpy_stream stream);
+
 /* Sample recycling (Sec. 5, "Samples recycling"): a pool of m particles
    collected after the mutation of every stage t = 1..T (particle of stage t
    distributed as p_t = L^beta_t pi / Z_t), taken together as draws from the

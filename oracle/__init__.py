@@ -98,6 +98,9 @@ _SIGS = {
     "ref_waveform": (C.c_int, [_P(Model), _P(Event), _D, _D]),
     "ref_loglike": (C.c_int, [_P(Model), _P(Event), C.c_int64, _D, _D, _D]),
     "ref_set_threads": (C.c_int, [C.c_int]),
+    "ref_nuts_mutate_local": (C.c_int, [_P(Model), _P(Event), C.c_int64, C.c_double, _D, _D, _D, _D,
+                                        C.c_double, C.c_int, C.c_int, C.c_uint64, C.c_uint32,
+                                        _P(NutsStats)]),
     "ref_fisher": (C.c_int, [_P(Model), _P(Event), C.c_int64, _D, _D]),
     "ref_local_metric": (C.c_int, [_P(Model), _P(Event), C.c_int64, _D, C.c_double, _D]),
     "ref_recycle_weights": (C.c_int, [C.c_int64, C.c_int, _D, _D, _D, _D]),
@@ -281,6 +284,26 @@ def nuts_mutate(model, event, beta, theta, lnl, grad, inv_mass, step, max_depth,
     evp = C.byref(event.ev) if event is not None else None
     _check(lib().ref_nuts_mutate(C.byref(model), evp, n, beta, _dp(theta), _dp(lnl), _dp(grad),
                                  _dp(im), step, max_depth, n_steps, key, ctr, st), "nuts_mutate")
+    stats = {
+        "accept_sum": np.array([s.accept_sum for s in st]),
+        "depth_sum": np.array([s.depth_sum for s in st]),
+        "n_leapfrog": np.array([s.n_leapfrog for s in st]),
+        "n_divergent": np.array([s.n_divergent for s in st]),
+    }
+    return theta, lnl, grad, stats
+
+
+def nuts_mutate_local(model, event, beta, theta, lnl, grad, inv_mass, step, max_depth, n_steps, key, ctr):
+    """nuts_mutate with one inverse mass matrix per particle (inv_mass [N][D][D])."""
+    theta = _f64(theta).copy()
+    lnl = _f64(lnl).copy()
+    grad = _f64(grad).copy()
+    n = theta.shape[0]
+    st = (NutsStats * n)()
+    im = _f64(inv_mass)
+    evp = C.byref(event.ev) if event is not None else None
+    _check(lib().ref_nuts_mutate_local(C.byref(model), evp, n, beta, _dp(theta), _dp(lnl), _dp(grad),
+                                       _dp(im), step, max_depth, n_steps, key, ctr, st), "nuts_mutate_local")
     stats = {
         "accept_sum": np.array([s.accept_sum for s in st]),
         "depth_sum": np.array([s.depth_sum for s in st]),

@@ -106,7 +106,8 @@ typedef struct {
   double alpha;                 /* target ESS fraction */
   int n_mut;                    /* NUTS transitions per stage */
   int max_depth;
-  int metric;                   /* 0: identity, eps = eps_scale * min_j sigma_j; 1: dense weighted covariance, eps = eps_scale */
+  int metric;                   /* 0: identity, eps = eps_scale * min_j sigma_j; 1: dense weighted covariance, eps = eps_scale;
+                                   2: per-particle local metric (ref_local_metric), eps = eps_scale */
   double eps_scale;
   int max_stages;
 } ref_smc_opts;
@@ -175,6 +176,13 @@ int ref_nuts_mutate(const ref_model* m, const ref_event* ev, int64_t n, double b
                     double* theta, double* lnl, double* grad, const double* inv_mass,
                     double step, int max_depth, int n_steps, uint64_t key, uint32_t ctr,
                     ref_nuts_stats* stats);
+
+/* As ref_nuts_mutate with one inverse mass matrix per particle
+   (inv_mass [N][D][D]: the local metric of Sec. 5). */
+int ref_nuts_mutate_local(const ref_model* m, const ref_event* ev, int64_t n, double beta,
+                          double* theta, double* lnl, double* grad, const double* inv_mass,
+                          double step, int max_depth, int n_steps, uint64_t key, uint32_t ctr,
+                          ref_nuts_stats* stats);
 
 /* Adaptive tempering step: beta_next, the incremental weights W (max 1),
    their ESS and the evidence increment dlnz = logsumexp(dbeta lnL) - ln N. */

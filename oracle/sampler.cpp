@@ -282,6 +282,78 @@ int ref_nuts_mutate(const ref_model* m, const ref_event* ev, int64_t n, double b
   return 0;
 }
 
+// As ref_nuts_mutate, each particle with its own inverse mass matrix
+// (inv_mass [N][D][D]): the local metric of Sec. 5, fixed through the call.
+int ref_nuts_mutate_local(const ref_model* m, const ref_event* ev, int64_t n, double beta, double* theta,
+                          double* lnl, double* grad, const double* inv_mass, double step, int max_depth,
+                          int n_steps, uint64_t key, uint32_t ctr, ref_nuts_stats* stats) {
+  if (max_depth < 0 || max_depth > kMaxDepth || !inv_mass) return -1;
+  Sampler s;
+  s.m = m;
+  s.ev = ev;
+  s.D = m->n_dim;
+  s.beta = beta;
+  const int D = s.D;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t i = 0; i < n; ++i) {
+    Sampler sp = s;
+    set_metric(sp, inv_mass + i * D * D);
+    Point cur;
+    for (int j = 0; j < D; ++j) cur.th[j] = theta[i * D + j];
+    sp.evaluate(cur);
+    ref_nuts_stats st = {0.0, 0, 0, 0};
+    for (int t = 0; t < n_steps; ++t)
+      sp.transition(cur, key, (uint32_t)i, ctr + (uint32_t)t, step, max_depth, &st);
+    for (int j = 0; j < D; ++j) {
+      theta[i * D + j] = cur.th[j];
+      grad[i * D + j] = cur.gl[j];
+    }
+    lnl[i] = cur.lnl;
+    if (stats) stats[i] = st;
+  }
+  return 0;
+}
+
+// Inverse of a symmetric positive-definite matrix through its Cholesky
+// factor (in place; the diagonal if the factorisation fails).
+static void spd_inverse(int D, double* a) {
+  std::vector<double> c(a, a + D * D), ci(D * D, 0.0);
+  bool ok = true;
+  for (int j = 0; j < D && ok; ++j) {
+    double d = c[j * D + j];
+    for (int k = 0; k < j; ++k) d -= c[j * D + k] * c[j * D + k];
+    if (!(d > 0.0) || !std::isfinite(d)) {
+      ok = false;
+      break;
+    }
+    c[j * D + j] = std::sqrt(d);
+    for (int i = j + 1; i < D; ++i) {
+      double t = c[i * D + j];
+      for (int k = 0; k < j; ++k) t -= c[i * D + k] * c[j * D + k];
+      c[i * D + j] = t / c[j * D + j];
+    }
+  }
+  if (!ok) {
+    for (int i = 0; i < D; ++i)
+      for (int j = 0; j < D; ++j) a[i * D + j] = i == j ? 1.0 / a[i * D + i] : 0.0;
+    return;
+  }
+  for (int j = 0; j < D; ++j) {  // C^-1 column by column (forward substitution)
+    ci[j * D + j] = 1.0 / c[j * D + j];
+    for (int i = j + 1; i < D; ++i) {
+      double t = 0.0;
+      for (int k = j; k < i; ++k) t -= c[i * D + k] * ci[k * D + j];
+      ci[i * D + j] = t / c[i * D + i];
+    }
+  }
+  for (int i = 0; i < D; ++i)  // M^-1 = C^-T C^-1
+    for (int j = 0; j < D; ++j) {
+      double t = 0.0;
+      for (int k = (i > j ? i : j); k < D; ++k) t += ci[k * D + i] * ci[k * D + j];
+      a[i * D + j] = t;
+    }
+}
+
 // Eq. (5)-(6): ESS of w_i = exp(dbeta (lnL_i - max)); bisection on dbeta.
 static double ess_at(int64_t n, const double* x, double db) {
   double s1 = 0.0, s2 = 0.0;
@@ -408,7 +480,7 @@ int ref_smc_run(const ref_model* m, const ref_event* ev, const ref_smc_opts* o, 
     l.swap(l2);
     double eps;
     const double* minv = nullptr;
-    if (o->metric == 1) {
+    if (o->metric == 1 || o->metric == 2) {
       eps = o->eps_scale;
       minv = cov.data();
     } else {
@@ -416,8 +488,17 @@ int ref_smc_run(const ref_model* m, const ref_event* ev, const ref_smc_opts* o, 
       for (int j = 0; j < D; ++j) smin = std::fmin(smin, std::sqrt(cov[j * D + j]));
       eps = o->eps_scale * smin;
     }
-    ref_nuts_mutate(m, ev, n, bn, th.data(), l.data(), g.data(), minv, eps, o->max_depth, o->n_mut, key,
-                    (uint32_t)t << 8, st.data());
+    if (o->metric == 2) {
+      // local metric of each resampled particle at the new temperature (Sec. 5)
+      std::vector<double> pm((size_t)n * D * D);
+      ref_local_metric(m, ev, n, th.data(), bn, pm.data());
+      for (int64_t i = 0; i < n; ++i) spd_inverse(D, pm.data() + i * D * D);
+      ref_nuts_mutate_local(m, ev, n, bn, th.data(), l.data(), g.data(), pm.data(), eps, o->max_depth, o->n_mut,
+                            key, (uint32_t)t << 8, st.data());
+    } else {
+      ref_nuts_mutate(m, ev, n, bn, th.data(), l.data(), g.data(), minv, eps, o->max_depth, o->n_mut, key,
+                      (uint32_t)t << 8, st.data());
+    }
     if (stages) {
       ref_stage& s = stages[t - 1];
       s.beta = bn;

@@ -208,6 +208,16 @@ class Context:
             return lnz.value, th, ll, rec, pth[:rows], pll[:rows]
         return lnz.value, th, ll, rec
 
+    def local_metric(self, theta, beta, want=("mass", "inv_mass", "chol")):
+        """Per-particle mass matrices (sharpy_local_metric): dict of [N][D][D] tensors."""
+        theta = _dev(theta, "theta")
+        n, d = theta.shape
+        out = {k: torch.empty((n, d, d), dtype=torch.float64, device=theta.device) for k in want}
+        check(lib().sharpy_local_metric(self._h, n, _ptr(theta), beta, _ptr(out.get("mass")),
+                                        _ptr(out.get("inv_mass")), _ptr(out.get("chol")), _stream()),
+              "sharpy_local_metric")
+        return out
+
     def status(self):
         return lib().sharpy_get_status(self._h)
 

@@ -18,7 +18,8 @@ LIB = os.path.join(OUT, "libsharpy.so")
 # (precision, detector count) so the persistent-kernel variants build in parallel.
 UNITS = [("context.cu", [], "context"), ("loglike.cu", [], "loglike"), ("smc.cu", [], "smc"),
          ("nuts.cu", [], "nuts"), ("run.cu", [], "run"), ("probe.cu", [], "probe"),
-         ("batch.cu", [], "batch"), ("recycle.cu", [], "recycle")] + [
+         ("batch.cu", [], "batch"), ("recycle.cu", [], "recycle"),
+         ("metric.cu", [], "metric")] + [
     ("nuts_inst.cu", [f"-DSHARPY_NUTS_PREC={p}", f"-DSHARPY_NUTS_NDET={d}"], f"nuts_p{p}_{d}")
     for p in (0, 1, 2) for d in (1, 2, 3)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -62,6 +62,8 @@ struct DevEvent {
   const double2* e64;        // [n_det][K] E = w conj(d) f^-7/6 (FP64)
   const float2* e32;         // [n_det][K] same, FP32
   const double* pref;        // [n_det][K] prefix sums of w f^-7/3
+  const double* p1;          // [n_det][kNBasis][K] prefix sums of w f^-7/3 B_m (Fisher), or null
+  const double* p2;          // [n_det][kNBasis (kNBasis + 1) / 2][K] ... B_m B_n, m <= n, or null
   DevDetector det[kMaxDet];
 };
 

@@ -39,6 +39,10 @@ static void free_event(sharpy_ctx* c) {
   cudaFree(c->d_e64);
   cudaFree(c->d_e32);
   cudaFree(c->d_pref);
+  cudaFree(c->d_p1);
+  cudaFree(c->d_p2);
+  c->d_p1 = c->d_p2 = nullptr;
+  c->ev.p1 = c->ev.p2 = nullptr;
   c->d_f = c->d_b64 = c->d_pref = nullptr;
   c->d_b32 = nullptr;
   c->d_b32lo = nullptr;
@@ -162,7 +166,7 @@ int sharpy_set_data(sharpy_ctx* c, int n_det, int64_t n_bins, double f_min, doub
   int rc = check_ctx(c, false);
   if (rc) return rc;
 
-  std::vector<double> f(K), b64(kNBasis * K), e64(2 * n_det * K), pref(n_det * K);
+  std::vector<double> f(K), b64(kNBasis * K), e64(2 * n_det * K), pref(n_det * K), wamp2(n_det * K);
   std::vector<float> b32(kNBasis * K), b32lo(kNBasis * K), e32(2 * n_det * K);
   for (int64_t k = 0; k < K; ++k) {
     double fk = f_min + (double)k * df;
@@ -191,6 +195,7 @@ int sharpy_set_data(sharpy_ctx* c, int n_det, int64_t n_bins, double f_min, doub
       e32[2 * i] = (float)e64[2 * i];
       e32[2 * i + 1] = (float)e64[2 * i + 1];
       double term = w * amp * amp;
+      wamp2[i] = term;
       double t = s + term;
       cmp += std::fabs(s) >= std::fabs(term) ? (s - t) + term : (term - t) + s;
       s = t;
@@ -238,7 +243,11 @@ int sharpy_set_data(sharpy_ctx* c, int n_det, int64_t n_bins, double f_min, doub
   ev.e64 = c->d_e64;
   ev.e32 = c->d_e32;
   ev.pref = c->d_pref;
+  ev.p1 = nullptr;
+  ev.p2 = nullptr;
   for (int a = 0; a < n_det; ++a) detector_geometry(det[a], ev.det[a]);
+  c->h_wamp2.swap(wamp2);
+  c->h_basis.swap(b64);
   c->has_data = true;
   return SHARPY_OK;
 }

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 struct sharpy_ctx {
@@ -26,6 +28,11 @@ struct sharpy_ctx {
   // pinned host staging for small readbacks
   double* h_pinned = nullptr;
   cudaStream_t last_stream = nullptr;
+  // host copies for the Fisher-information prefix tables (built on first use)
+  std::vector<double> h_wamp2;  // [n_det][K] w f^-7/3
+  std::vector<double> h_basis;  // [kNBasis][K]
+  double* d_p1 = nullptr;       // [n_det][kNBasis][K] prefix sums of w f^-7/3 B_m
+  double* d_p2 = nullptr;       // [n_det][kNBasis (kNBasis + 1) / 2][K] prefix sums of w f^-7/3 B_m B_n
   // NUTS slot count picked by the autotuner for (tuned_n, tuned_prec)
   int tuned_slots = 0;
   int64_t tuned_n = -1;

@@ -24,7 +24,7 @@ def gauss_lnz(beta, mu, sig, lo, hi):
     return out
 
 
-@pytest.mark.parametrize("metric", [0, 1])
+@pytest.mark.parametrize("metric", [0, 1, 2])
 def test_smc_gaussian_evidence(metric):
     """Gaussian likelihood, uniform box prior: ln Z and every stage's ln Z_beta against the closed
     form (Sec. 3.1 Eqs. 7-8), over 8 seeds."""
@@ -86,6 +86,23 @@ def test_nuts_stationarity(dense):
     # returned ln L / grad belong to the returned positions
     l3, g3 = oracle.loglike(model, None, out)
     assert np.allclose(l2, l3, rtol=1e-12, atol=1e-12) and np.allclose(g2, g3, rtol=1e-12, atol=1e-12)
+
+
+def test_nuts_per_particle_metric_stationarity():
+    """Each particle with its own (random, fixed) dense metric: one transition from the target still
+    yields the target (KS per coordinate)."""
+    d = 2
+    model = helpers.gaussmix_model([-10.0] * d, [10.0] * d, [0.0], [[0.0] * d], [[1.0, 0.3]])
+    rng = np.random.default_rng(18)
+    n = 20000
+    th = rng.standard_normal((n, d)) * np.array([1.0, 0.3])
+    lnl, g = oracle.loglike(model, None, th)
+    a = rng.standard_normal((n, d, d)) * 0.5
+    minv = np.einsum("nij,nkj->nik", a, a) + np.diag([0.5, 0.05])[None]
+    out, l2, g2, st = oracle.nuts_mutate_local(model, None, 1.0, th, lnl, g, minv, 0.4, 8, 1, key=19, ctr=0)
+    assert stats.kstest(out[:, 0], "norm").pvalue > 1e-3
+    assert stats.kstest(out[:, 1] / 0.3, "norm").pvalue > 1e-3
+    assert np.mean(np.abs(out - th)) > 0.1
 
 
 def test_nuts_long_chain_moments():
