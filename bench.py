@@ -276,6 +276,9 @@ def main_batch(args):
         torch.cuda.synchronize()
 
     ws = inputs.batch64()
+    if args.metric is not None:
+        for w in ws:
+            w.metric = args.metric
     base = multirank.event_seed(rank) * 1000
     ctxs = [api.make_event(w, seed=base + i, device=local)[0] for i, w in enumerate(ws)]
     w0 = ws[0]
@@ -344,6 +347,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="bbh11", choices=["tiny", "bbh11", "bbh11_long", "bns", "batch64"])
     ap.add_argument("--mode", default="smc", choices=["smc", "loglike"])
+    ap.add_argument("--metric", type=int, default=None, choices=[0, 1, 2],
+                    help="NUTS metric (default: the workload's): 0 identity, 1 covariance, 2 per-particle local")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -375,6 +380,8 @@ def main():
         return multirank.reduce_scalar(x, "sum", world, device="cuda")
 
     w = inputs.bbh11()
+    if args.metric is not None:
+        w.metric = args.metric
     ctx, th_inj, data = api.make_event(w, seed=multirank.event_seed(rank), device=local)
     run_args = (w.n_particles, w.alpha, w.n_mut, w.max_depth, w.metric, w.eps_scale)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
@@ -507,7 +514,10 @@ def main():
                "data": "synthetic",
                "config": {"workload": "bbh11: 11-D aligned-spin TaylorF2, 3 detectors, 8 s at 1/8 Hz "
                                       "(8033 bins, 20-1024 Hz), 2048 particles, NUTS depth 6, alpha 0.5, "
-                                      "2 transitions/stage, identity metric; one step = one full SMC run",
+                                      "2 transitions/stage, "
+                                      + {0: "identity metric", 1: "covariance metric",
+                                         2: "per-particle local metric"}[w.metric]
+                                      + "; one step = one full SMC run",
                           "precision": args.precision, "l2": "flushed (256 MB write) between steps",
                           "parallelism": f"one independent event per GPU x {world}",
                           "stages_per_run": n_stages},

@@ -114,7 +114,8 @@ typedef struct {
   double alpha;        /* target ESS fraction, Eq. (6)                               */
   int n_mut;           /* NUTS transitions per stage                                 */
   int max_depth;       /* NUTS tree depth limit (<= SHARPY_MAX_DEPTH)                */
-  int metric;          /* 0: identity, step = eps_scale * min_j sigma_j; 1: weighted covariance, step = eps_scale */
+  int metric;          /* 0: identity, step = eps_scale * min_j sigma_j; 1: weighted covariance, step = eps_scale;
+                          2: per-particle local metric (sharpy_local_metric at the stage's beta), step = eps_scale */
   double eps_scale;
   int precision;       /* SHARPY_FP64 / SHARPY_MIXED / SHARPY_MIXED_SPLIT            */
   int max_stages;
@@ -186,6 +187,15 @@ int sharpy_nuts_mutate(sharpy_ctx* ctx, int64_t n, double beta, double* theta, d
                        double* grad, const double* inv_mass, double step, int max_depth, int n_steps,
                        uint64_t key, uint64_t ctr, int precision, sharpy_nuts_stats* stats,
                        sharpy_stream stream);
+
+/* sharpy_nuts_mutate with one metric per particle (the local metric of
+   Sec. 5, e.g. from sharpy_local_metric): inv_mass [N][D][D] = M_i^-1 and
+   chol [N][D][D] = L_i lower triangular with L_i L_i^T = M_i^-1 (device,
+   FP64), fixed through the call. */
+int sharpy_nuts_mutate_local(sharpy_ctx* ctx, int64_t n, double beta, double* theta, double* lnl,
+                             double* grad, const double* inv_mass, const double* chol, double step,
+                             int max_depth, int n_steps, uint64_t key, uint64_t ctr, int precision,
+                             sharpy_nuts_stats* stats, sharpy_stream stream);
 
 /* One tempering step (Sec. 3, Eqs. 4-8): the increment dbeta solving
    ESS = alpha N (the largest FP64-verified dbeta with ESS >= alpha N, within

@@ -156,6 +156,17 @@ class Context:
               "sharpy_nuts_mutate")
         return st
 
+    def nuts_mutate_local(self, beta, theta, lnl, grad, inv_mass, chol, step, max_depth, n_steps, key, ctr,
+                          precision="mixed", stats=True):
+        """nuts_mutate with one metric per particle (inv_mass, chol: [N][D][D] device)."""
+        n = theta.shape[0]
+        st = torch.empty(n * STATS_DTYPE.itemsize, dtype=torch.uint8, device=theta.device) if stats else None
+        check(lib().sharpy_nuts_mutate_local(self._h, n, beta, _ptr(_dev(theta, "theta")), _ptr(_dev(lnl, "lnl")),
+                                             _ptr(_dev(grad, "grad")), _ptr(_dev(inv_mass, "inv_mass")),
+                                             _ptr(_dev(chol, "chol")), step, max_depth, n_steps, key, ctr,
+                                             _prec(precision), _ptr(st), _stream()), "sharpy_nuts_mutate_local")
+        return st
+
     @staticmethod
     def stats_to_numpy(st):
         return np.frombuffer(st.cpu().numpy().tobytes(), dtype=STATS_DTYPE)

@@ -23,6 +23,10 @@ using namespace sharpy;
 
 namespace sharpy {
 
+int ensure_fisher_tables(sharpy_ctx* c);
+int enqueue_local_metric(sharpy_ctx* c, int64_t n, const double* theta, const double* beta_ptr, double beta,
+                         double* mass, double* minv, double* chol, cudaStream_t s);
+
 constexpr int kBatchRec = 9;  // beta, ess, dlnz, eps, accept, depth, leapfrogs, divergent, active bins
 constexpr int kRoundsPerCheck = 4;
 
@@ -102,6 +106,8 @@ struct sharpy_batch {
   double *th = nullptr, *gr = nullptr, *ll = nullptr, *th0 = nullptr, *g0 = nullptr, *l0 = nullptr;
   double *w = nullptr, *beta = nullptr, *bnext = nullptr, *dlnz = nullptr, *ess = nullptr, *sumw = nullptr;
   double *lnz = nullptr, *cov = nullptr, *rec = nullptr, *tot = nullptr;
+  double *pminv = nullptr, *pchol = nullptr;  // per-particle metric (option 2): [N_e][D_e][D_e] per event
+  std::vector<int64_t> moff;                   // offset of event e in pminv / pchol
   unsigned long long* csum = nullptr;
   int32_t* anc = nullptr;
   sharpy_nuts_stats* st = nullptr;
@@ -148,7 +154,13 @@ int slot_index(int slots) {
 
 int enqueue_round_stage(sharpy_batch* b, cudaStream_t s) {
   StageArgs none{};
-  return enqueue_stage_kernels(none, b->d_stage, b->ne, b->max_n, b->max_d, true, true, 0ull, s);
+  int rc = enqueue_stage_kernels(none, b->d_stage, b->ne, b->max_n, b->max_d, true, true, 0ull, s);
+  if (rc || b->opt.metric != 2) return rc;
+  // local metric of every event's resampled particles at its new beta
+  for (int e = 0; e < b->ne && !rc; ++e)
+    rc = enqueue_local_metric(b->ctx[e], b->n[e], b->th + b->doff[e], b->beta + e, 0.0, nullptr,
+                              b->pminv + b->moff[e], b->pchol + b->moff[e], s);
+  return rc;
 }
 
 int enqueue_round_nuts(sharpy_batch* b, const NutsArgs* args, int slots, cudaStream_t s) {
@@ -198,7 +210,7 @@ int sharpy_batch_create(sharpy_batch** out, sharpy_ctx* const* events, int n_eve
   if (!out || !events || !n_particles || !o || n_events < 1 || n_events > (1 << 16)) return SHARPY_EINVAL;
   *out = nullptr;
   if (!(o->alpha > 0.0 && o->alpha <= 1.0) || o->n_mut < 0 || o->max_depth < 0 || o->max_depth > SHARPY_MAX_DEPTH ||
-      o->max_stages < 1 || !(o->eps_scale > 0.0) || (o->metric != 0 && o->metric != 1) ||
+      o->max_stages < 1 || !(o->eps_scale > 0.0) || (o->metric != 0 && o->metric != 1 && o->metric != 2) ||
       (o->precision != SHARPY_FP64 && o->precision != SHARPY_MIXED && o->precision != SHARPY_MIXED_SPLIT))
     return SHARPY_EINVAL;
   sharpy_batch* b = new sharpy_batch();
@@ -231,6 +243,19 @@ int sharpy_batch_create(sharpy_batch** out, sharpy_ctx* const* events, int n_eve
   }
   b->device = events[0]->device;
   const int E = n_events;
+  int64_t nm = 0;  // per-particle metric entries
+  for (int e = 0; e < E; ++e) {
+    b->moff.push_back(nm);
+    nm += b->n[e] * b->D[e] * b->D[e];
+    if (o->metric == 2 && events[e]->model.model == SHARPY_MODEL_TAYLORF2) {
+      const int rc = ensure_fisher_tables(events[e]);
+      if (rc) {
+        delete b;
+        return rc;
+      }
+    }
+  }
+  if (o->metric != 2) nm = 0;
   const int64_t N = b->n_total, ND = b->nd_total, S = o->max_stages;
   const int DD = b->max_d * b->max_d;
   // CTA maps: events by decreasing cost (bins x detectors), each event's CTAs in order
@@ -256,6 +281,7 @@ int sharpy_batch_create(sharpy_batch** out, sharpy_ctx* const* events, int n_eve
   add(5 * (size_t)E, 8); add(2 * (size_t)E, 8); add((size_t)E * DD, 8); add((size_t)E * S * kBatchRec, 8);
   add(2 * (size_t)E, 8);                    // tot
   add(3 * (size_t)E, 4);                    // active, done, stage
+  add(nm, 8); add(nm, 8);                   // per-particle metric
   add(E, sizeof(StageArgs)); add(E, sizeof(NutsArgs)); add(E, sizeof(NutsArgs));
   for (int i = 0; i < kNumSlotChoices; ++i) add(maps[i].size(), sizeof(int2));
   if (cudaSetDevice(b->device) != cudaSuccess || cudaMalloc((void**)&b->d_buf, bytes) != cudaSuccess ||
@@ -286,6 +312,8 @@ int sharpy_batch_create(sharpy_batch** out, sharpy_ctx* const* events, int n_eve
   b->rec = carve<double>(p, (size_t)E * S * kBatchRec);
   b->tot = carve<double>(p, 2 * (size_t)E);
   b->flags = carve<int>(p, 3 * (size_t)E);
+  b->pminv = carve<double>(p, nm);
+  b->pchol = carve<double>(p, nm);
   b->active = b->flags;
   b->done = b->flags + E;
   b->stage = b->flags + 2 * E;
@@ -336,7 +364,9 @@ int sharpy_batch_create(sharpy_batch** out, sharpy_ctx* const* events, int n_eve
     U.grad = A.grad;
     U.beta_ptr = b->beta + e;
     U.minv = o->metric == 1 ? A.cov : nullptr;
-    U.cov_step = o->metric == 1 ? nullptr : A.cov;
+    U.cov_step = o->metric == 0 ? A.cov : nullptr;
+    U.pminv = o->metric == 2 ? b->pminv + b->moff[e] : nullptr;
+    U.pchol = o->metric == 2 ? b->pchol + b->moff[e] : nullptr;
     U.step = o->eps_scale;
     U.max_depth = o->max_depth;
     U.n_steps = o->n_mut;

@@ -37,7 +37,7 @@ int launch_nuts(int precision, int ndet, int slots, const NutsArgs& A, unsigned 
 int enqueue_nuts(sharpy_ctx* c, int64_t n, const double* beta_ptr, double beta, double* theta, double* lnl,
                  double* grad, const double* inv_mass, const double* cov_step, double step, int max_depth,
                  int n_steps, uint64_t key, uint32_t ctr, int precision, sharpy_nuts_stats* stats, cudaStream_t s,
-                 int slots) {
+                 int slots, const double* pminv, const double* pchol) {
   NutsArgs A;
   A.m = c->model;
   A.ev = c->ev;
@@ -64,6 +64,8 @@ int enqueue_nuts(sharpy_ctx* c, int64_t n, const double* beta_ptr, double beta, 
     slots = n >= (int64_t)16 * 2 * sms * 3 / 4 ? 16 : 8;
   }
   const int nd = c->model.model == SHARPY_MODEL_TAYLORF2 ? c->ev.n_det : 1;
+  A.pminv = pminv;
+  A.pchol = pchol;
   A.batch = nullptr;
   A.cta_map = nullptr;
   A.active = nullptr;
@@ -87,5 +89,24 @@ extern "C" int sharpy_nuts_mutate(sharpy_ctx* c, int64_t n, double beta, double*
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
   return enqueue_nuts(c, n, nullptr, beta, theta, lnl, grad, inv_mass, nullptr, step, max_depth, n_steps, key,
-                      (uint32_t)ctr, precision, stats, s, 0);
+                      (uint32_t)ctr, precision, stats, s, 0, nullptr, nullptr);
+}
+
+extern "C" int sharpy_nuts_mutate_local(sharpy_ctx* c, int64_t n, double beta, double* theta, double* lnl,
+                                        double* grad, const double* inv_mass, const double* chol, double step,
+                                        int max_depth, int n_steps, uint64_t key, uint64_t ctr, int precision,
+                                        sharpy_nuts_stats* stats, sharpy_stream stream) {
+  int rc = check_ctx(c, true);
+  if (rc) return rc;
+  if (n < 0 || n > ((int64_t)1 << 31) - 1) return SHARPY_EINVAL;
+  if (n == 0) return SHARPY_OK;
+  if (!theta || !lnl || !grad || !inv_mass || !chol || !(step > 0.0) || !isfinite(step) || max_depth < 0 ||
+      max_depth > kMaxDepth || n_steps < 0 || !(beta >= 0.0 && beta <= 1.0))
+    return SHARPY_EINVAL;
+  if (precision != SHARPY_FP64 && precision != SHARPY_MIXED && precision != SHARPY_MIXED_SPLIT)
+    return SHARPY_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  return enqueue_nuts(c, n, nullptr, beta, theta, lnl, grad, nullptr, nullptr, step, max_depth, n_steps, key,
+                      (uint32_t)ctr, precision, stats, s, 0, inv_mass, chol);
 }

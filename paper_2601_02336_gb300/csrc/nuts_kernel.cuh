@@ -66,6 +66,8 @@ struct NutsArgs {
   const double* beta_ptr;
   double beta;
   const double* minv;      // [D][D] or null
+  const double* pminv;     // [n][D][D] per-particle metric (with pchol), or null
+  const double* pchol;
   const double* cov_step;  // identity metric with step = eps_scale * min sqrt(diag cov)
   double step;
   int max_depth;
@@ -89,8 +91,8 @@ template <int SLOTS, class VT>
 struct NutsShared {
   double pos[P_COUNT][kMaxDim][SLOTS];
   VT vec[F_COUNT][kMaxDim][SLOTS];
-  VT minv[kMaxDim][kMaxDim];
-  VT chol[kMaxDim][kMaxDim];
+  VT minv[kMaxDim][kMaxDim][SLOTS];  // each slot's metric (a copy of the shared one, or its own)
+  VT chol[kMaxDim][kMaxDim][SLOTS];
   long long lokey[kMaxDim], hikey[kMaxDim];  // order keys of the prior box (see okey)
   double eps, beta;
   double lp_const;  // sum of the prior's constant log terms
@@ -169,6 +171,8 @@ struct Nuts {
   int D;
   __device__ Nuts(const NutsArgs& a, NutsShared<SLOTS, VT>& sh, int slot) : A(a), S(sh), s(slot), D(a.m.n_dim) {}
   __device__ VT& V(int f, int d) { return S.vec[f][d][s]; }
+  __device__ VT& MI(int i, int j) { return S.minv[i][j][s]; }
+  __device__ VT& CH(int i, int j) { return S.chol[i][j][s]; }
   __device__ double& X(int f, int d) { return S.pos[f][d][s]; }
 
   // v = Minv r for the momentum stored in field f
@@ -176,11 +180,11 @@ struct Nuts {
     if (S.metric_kind == METRIC_IDENTITY) {
       for (int i = 0; i < D; ++i) v[i] = V(f, i);
     } else if (S.metric_kind == METRIC_DIAGONAL) {
-      for (int i = 0; i < D; ++i) v[i] = S.minv[i][i] * V(f, i);
+      for (int i = 0; i < D; ++i) v[i] = MI(i, i) * V(f, i);
     } else {
       for (int i = 0; i < D; ++i) {
         VT acc = VT(0);
-        for (int j = 0; j < D; ++j) acc += S.minv[i][j] * V(f, j);
+        for (int j = 0; j < D; ++j) acc += MI(i, j) * V(f, j);
         v[i] = acc;
       }
     }
@@ -249,7 +253,7 @@ struct Nuts {
         if (flips & 1) {
           VT v[kMaxDim];
           velocity(F_NR, v);
-          V(F_NR, i) = V(F_NR, i) - VT(2) * v[i] / S.minv[i][i];
+          V(F_NR, i) = V(F_NR, i) - VT(2) * v[i] / MI(i, i);
         }
       }
     }
@@ -293,8 +297,8 @@ struct Nuts {
     // r ~ N(0, M), M = Minv^{-1} = (L L^T)^{-1}: solve L^T r = z
     for (int i = D - 1; i >= 0; --i) {
       VT acc = z[i];
-      for (int j = i + 1; j < D; ++j) acc -= S.chol[j][i] * V(F_LR, j);
-      V(F_LR, i) = acc / S.chol[i][i];
+      for (int j = i + 1; j < D; ++j) acc -= CH(j, i) * V(F_LR, j);
+      V(F_LR, i) = acc / CH(i, i);
     }
     // U and grad U at the current point
     double x[kMaxDim];
@@ -528,10 +532,10 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(const __grid_c
       for (int j = 0; j < D; ++j) {
         if (i != j && mi[i][j] != 0.0) diag = false;
         if (mi[i][j] != (i == j ? 1.0 : 0.0)) ident = false;
-        S.minv[i][j] = (VT)mi[i][j];
-        S.chol[i][j] = (VT)ch[i][j];
+        S.minv[i][j][0] = (VT)mi[i][j];
+        S.chol[i][j][0] = (VT)ch[i][j];
       }
-    S.metric_kind = ident ? METRIC_IDENTITY : (diag ? METRIC_DIAGONAL : METRIC_DENSE);
+    S.metric_kind = A.pminv ? METRIC_DENSE : ident ? METRIC_IDENTITY : (diag ? METRIC_DIAGONAL : METRIC_DENSE);
     for (int i = 0; i < D; ++i) {
       S.lokey[i] = okey(A.m.lo[i]);
       S.hikey[i] = okey(A.m.hi[i]);
@@ -552,6 +556,13 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(const __grid_c
     S.beta = A.beta_ptr ? *A.beta_ptr : A.beta;
   }
   __syncthreads();
+  // every slot starts from the shared metric (per-particle metrics replace it below)
+  for (int e = threadIdx.x; e < kMaxDim * kMaxDim * (SLOTS - 1); e += blockDim.x) {
+    const int ij = e / (SLOTS - 1), k = 1 + e % (SLOTS - 1);
+    S.minv[ij / kMaxDim][ij % kMaxDim][k] = S.minv[ij / kMaxDim][ij % kMaxDim][0];
+    S.chol[ij / kMaxDim][ij % kMaxDim][k] = S.chol[ij / kMaxDim][ij % kMaxDim][0];
+  }
+  __syncthreads();
 
   Slot<VT> sl;
   bool active = false;
@@ -568,6 +579,15 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(const __grid_c
         nu.V(F_PGL, i) = (VT)A.grad[sl.pid * D + i];
       }
       sl.lnl_p = A.lnl[sl.pid];
+      if (A.pminv) {
+        const double* pm = A.pminv + sl.pid * D * D;
+        const double* pc = A.pchol + sl.pid * D * D;
+        for (int i = 0; i < D; ++i)
+          for (int j = 0; j < D; ++j) {
+            nu.MI(i, j) = (VT)pm[i * D + j];
+            nu.CH(i, j) = (VT)pc[i * D + j];
+          }
+      }
       sl.done = 0;
       active = nu.advance(sl, false, nullptr, 0.0, nullptr);
     }

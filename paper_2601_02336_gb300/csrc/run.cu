@@ -14,7 +14,9 @@ int enqueue_stage(sharpy_ctx* c, int64_t n, double* theta, double* lnl, double* 
 int enqueue_nuts(sharpy_ctx* c, int64_t n, const double* beta_ptr, double beta, double* theta, double* lnl,
                  double* grad, const double* inv_mass, const double* cov_step, double step, int max_depth,
                  int n_steps, uint64_t key, uint32_t ctr, int precision, sharpy_nuts_stats* stats, cudaStream_t s,
-                 int slots);
+                 int slots, const double* pminv, const double* pchol);
+int enqueue_local_metric(sharpy_ctx* c, int64_t n, const double* theta, const double* beta_ptr, double beta,
+                         double* mass, double* minv, double* chol, cudaStream_t s);
 
 // Per-stage record: [beta, ess, dlnz, eps, accept_sum, depth_sum, n_leapfrog, n_divergent, active_bins]
 constexpr int kRec = 9;
@@ -63,7 +65,7 @@ extern "C" int sharpy_smc_run(sharpy_ctx* c, const sharpy_smc_options* o, uint64
   if (rc) return rc;
   if (!o || !lnz || o->n_particles < 1 || o->n_particles > ((int64_t)1 << 20) || !(o->alpha > 0.0 && o->alpha <= 1.0) ||
       o->n_mut < 0 || o->max_depth < 0 || o->max_depth > SHARPY_MAX_DEPTH || o->max_stages < 1 ||
-      !(o->eps_scale > 0.0) || (o->metric != 0 && o->metric != 1) ||
+      !(o->eps_scale > 0.0) || (o->metric != 0 && o->metric != 1 && o->metric != 2) ||
       (o->precision != SHARPY_FP64 && o->precision != SHARPY_MIXED && o->precision != SHARPY_MIXED_SPLIT))
     return SHARPY_EINVAL;
   const int64_t n = o->n_particles;
@@ -73,8 +75,9 @@ extern "C" int sharpy_smc_run(sharpy_ctx* c, const sharpy_smc_options* o, uint64
   // run buffers: theta, grad [N][D], lnl [N], stats [N], scalars, cov, record;
   // copies of theta, grad, lnl for the autotuner's trials when it has to run
   const bool tune = !(c->tuned_slots && c->tuned_n == n && c->tuned_prec == o->precision);
+  const bool local = o->metric == 2;  // per-particle metric: [N][D][D] inverse and Cholesky factor
   size_t bytes = (size_t)n * (2 * D + 1) * sizeof(double) * (tune ? 2 : 1) + (size_t)n * sizeof(sharpy_nuts_stats) +
-                 (8 + D * D + kRec) * sizeof(double);
+                 (8 + D * D + kRec) * sizeof(double) + (local ? 2 * (size_t)n * D * D * sizeof(double) : 0);
   char* buf = nullptr;
   SHARPY_CUDA_TRY(cudaMallocAsync((void**)&buf, bytes, s));
   double* th = (double*)buf;
@@ -89,6 +92,8 @@ extern "C" int sharpy_smc_run(sharpy_ctx* c, const sharpy_smc_options* o, uint64
   double* cov = sc + 8;
   double* rec = cov + D * D;
   double* trial = rec + kRec;  // [N][D] theta, [N][D] grad, [N] lnl (autotuner)
+  double* pminv = trial + (tune ? (size_t)n * (2 * D + 1) : 0);
+  double* pchol = pminv + (size_t)n * D * D;
   int out = SHARPY_OK;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evr = nullptr;
   auto fail = [&](int code) {
@@ -116,14 +121,18 @@ extern "C" int sharpy_smc_run(sharpy_ctx* c, const sharpy_smc_options* o, uint64
                        beta_state, s);
     if (rc) return fail(rc);
     const double* minv = o->metric == 1 ? cov : nullptr;
-    const double* cov_step = o->metric == 1 ? nullptr : cov;
+    const double* cov_step = o->metric == 0 ? cov : nullptr;
+    if (local && (rc = enqueue_local_metric(c, n, th, beta_state, 0.0, nullptr, pminv, pchol, s))) return fail(rc);
+    const double* pm = local ? pminv : nullptr;
+    const double* pc = local ? pchol : nullptr;
     if (t == 1 && tune) {
       // pick the slot count on this stage: one transition on copies of the particles
       auto go = [&](int slots, cudaStream_t ts) -> int {
         SHARPY_CUDA_TRY(cudaMemcpyAsync(trial, th, (size_t)n * (2 * D + 1) * sizeof(double),
                                         cudaMemcpyDeviceToDevice, ts));
         return enqueue_nuts(c, n, beta_state, 0.0, trial, trial + 2 * n * D, trial + n * D, minv, cov_step,
-                            o->eps_scale, o->max_depth, 1, key, (uint32_t)t << 8, o->precision, st, ts, slots);
+                            o->eps_scale, o->max_depth, 1, key, (uint32_t)t << 8, o->precision, st, ts, slots, pm,
+                            pc);
       };
       TuneCandidate cands[kNumSlotChoices];
       for (int i = 0; i < kNumSlotChoices; ++i) cands[i].slots = kSlotChoices[i];
@@ -135,7 +144,7 @@ extern "C" int sharpy_smc_run(sharpy_ctx* c, const sharpy_smc_options* o, uint64
     }
     if (o->timing) cudaEventRecord(ev0, s);
     rc = enqueue_nuts(c, n, beta_state, 0.0, th, ll, gr, minv, cov_step, o->eps_scale, o->max_depth, o->n_mut, key,
-                      (uint32_t)t << 8, o->precision, st, s, 0);
+                      (uint32_t)t << 8, o->precision, st, s, 0, pm, pc);
     if (rc) return fail(rc);
     if (o->timing) cudaEventRecord(ev1, s);
     if (o->pool_theta && o->pool_lnl && (int64_t)t * n <= o->pool_cap) {

@@ -54,13 +54,15 @@ def test_batch_matches_separate_runs(precision):
     assert [r["lnz"] for r in res2] == [r["lnz"] for r in res]
 
 
-def test_batch_covariance_metric_single_detector():
-    """Two single-detector events (different noise) with the weighted-covariance metric."""
+@pytest.mark.parametrize("metric", [1, 2])
+def test_batch_dense_metrics_single_detector(metric):
+    """Two single-detector events (different noise) with the weighted-covariance metric (1) and the
+    per-particle local metric (2)."""
     G.require_gpu()
     ws = [inputs.tiny(), inputs.tiny()]
     ctxs = [api.make_event(w, seed=i)[0] for i, w in enumerate(ws)]
     keys = [5, 6]
-    kw = dict(alpha=0.5, n_mut=2, max_depth=5, metric=1, eps_scale=0.5, precision="fp64", max_stages=200)
+    kw = dict(alpha=0.5, n_mut=2, max_depth=5, metric=metric, eps_scale=0.5, precision="fp64", max_stages=200)
     b = api.Batch(ctxs, [w.n_particles for w in ws], **kw)
     res, _ = b.run(keys)
     _check_against_runs(b, ws, ctxs, keys, res, **kw)

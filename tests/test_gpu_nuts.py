@@ -30,11 +30,12 @@ def _gm(d=3, dense=False):
     return cfg, model, np.array(hi) - np.array(lo)
 
 
-def _compare(th_g, l_g, st_g, th_o, l_o, g_o, st_o, wid, frac=0.95, tol=1e-7):
+def _compare(th_g, l_g, st_g, th_o, l_o, g_o, st_o, wid, frac=0.95, tol=1e-7, lf_frac=1.0):
     dev = np.max(np.abs(th_g - th_o) / wid[None, :], axis=1)
     match = dev < tol
     assert match.mean() >= frac, (match.mean(), np.sort(dev)[-5:])
-    assert np.array_equal(st_g["n_leapfrog"][match], st_o["n_leapfrog"][match])
+    same_lf = st_g["n_leapfrog"][match] == st_o["n_leapfrog"][match]
+    assert same_lf.mean() >= lf_frac, same_lf.mean()
     # ln L differs by summation order (~1e-7) plus grad . (theta_gpu - theta_oracle)
     slack = 1e-6 + 1e-9 * np.abs(l_o) + 2.0 * np.abs(np.sum(g_o * (th_g - th_o), axis=1))
     assert np.all(np.abs(l_g - l_o)[match] <= slack[match])
@@ -139,3 +140,47 @@ def test_nuts_edge_cases():
     out = t.cpu().numpy()
     assert np.all(out >= -6.0) and np.all(out <= 6.0)
     assert ctx.status() == 0
+
+
+def test_nuts_per_particle_metric_gaussmix_matches_oracle():
+    """One fixed dense metric per particle (the same input arrays on both sides)."""
+    G.require_gpu()
+    cfg, model, wid = _gm(3)
+    ctx = api.Context(cfg)
+    n = 800
+    rng = np.random.default_rng(31)
+    th = rng.uniform(-3, 3, size=(n, 3))
+    lnl, g = oracle.loglike(model, None, th)
+    a = rng.standard_normal((n, 3, 3)) * 0.3
+    minv = np.einsum("nij,nkj->nik", a, a) + np.diag([0.6, 0.4, 0.3])[None]
+    chol = np.linalg.cholesky(minv)
+    ref = oracle.nuts_mutate_local(model, None, 0.7, th, lnl, g, minv, 0.4, 6, 2, key=23, ctr=3)
+    t, l, gg = G.to_dev(th), G.to_dev(lnl), G.to_dev(g)
+    st = ctx.nuts_mutate_local(0.7, t, l, gg, G.to_dev(minv), G.to_dev(chol), 0.4, 6, 2, key=23, ctr=3,
+                               precision="fp64")
+    _compare(t.cpu().numpy(), l.cpu().numpy(), api.Context.stats_to_numpy(st), ref[0], ref[1], ref[2], ref[3],
+             wid, frac=0.99)
+
+
+def test_nuts_local_metric_taylorf2_matches_oracle():
+    """The local metric of Sec. 5 computed on each side (GPU: sharpy_local_metric; oracle: its Fisher
+    information and an inverse), then one NUTS call with it. In physical units the mass matrix has a
+    condition number near 1e10, so the two inverses agree only to ~1e-6 relative: an occasional U-turn test
+    then falls differently (same end point, another leapfrog count)."""
+    G.require_gpu()
+    w = inputs.tiny()
+    ev, ctx, th_inj, _ = G.event_pair(w)
+    model = helpers.oracle_model(w)
+    n = 100
+    th = np.vstack([inputs.ball(w, th_inj, n // 2, 3, rel=2e-3), inputs.prior_draws(w, n - n // 2, 4)])
+    lnl, g = oracle.loglike(model, ev, th)
+    wid = G.width(w)
+    for beta in (0.05, 1.0):
+        minv_ref = np.linalg.inv(oracle.local_metric(model, ev, th, beta))
+        ref = oracle.nuts_mutate_local(model, ev, beta, th, lnl, g, minv_ref, 0.5, 5, 2, key=35, ctr=9)
+        t, l, gg = G.to_dev(th), G.to_dev(lnl), G.to_dev(g)
+        met = ctx.local_metric(t, beta, want=("inv_mass", "chol"))
+        st = ctx.nuts_mutate_local(beta, t, l, gg, met["inv_mass"], met["chol"], 0.5, 5, 2, key=35, ctr=9,
+                                   precision="fp64")
+        _compare(t.cpu().numpy(), l.cpu().numpy(), api.Context.stats_to_numpy(st), ref[0], ref[1], ref[2],
+                 ref[3], wid, frac=0.9, lf_frac=0.9)

@@ -107,3 +107,39 @@ def test_run_bimodal11_analytic_evidence():
         assert min(fracs) > 0.05 and max(fracs) < 0.95, (prec, fracs)
         assert abs(np.mean(fracs) - 0.5) < 0.2, (prec, fracs)
         assert abs(np.mean(lnzs) - truth) < 4 * _se(lnzs) + 0.1, (prec, lnzs, truth)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_run_local_metric_gaussian_evidence(precision):
+    """Per-particle local metric (metric 2) on a Gaussian likelihood: analytic ln Z (for one Gaussian
+    component the metric is constant, so the NUTS kernel is exactly invariant)."""
+    G.require_gpu()
+    mu, sig = [1.0, -2.0, 0.5], [0.5, 1.0, 0.3]
+    lo, hi = [-10.0] * 3, [10.0] * 3
+    ctx = api.Context(api.gaussmix_config(lo, hi, [0.0], [mu], [sig]))
+    truth = gauss_lnz(1.0, mu, sig, lo, hi)
+    lnzs = []
+    for seed in range(8):
+        lnz, th, lnl, rec = ctx.smc_run(1024, 0.5, 2, 5, 2, 0.5, key=1700 + seed, precision=precision)
+        lnzs.append(lnz)
+        assert np.allclose(th.cpu().numpy().mean(0), mu, atol=0.1)
+    assert abs(np.mean(lnzs) - truth) < 4 * _se(lnzs) + 0.02
+    assert ctx.status() == 0
+
+
+def test_run_local_metric_vs_oracle():
+    """Metric 2 on the single-detector TaylorF2 workload: GPU FP64 runs against oracle runs (ln Z within two
+    combined standard errors); stage 1 (before any mutation) identical."""
+    G.require_gpu()
+    w = inputs.tiny()
+    ev, ctx, th_inj, _ = G.event_pair(w)
+    model = helpers.oracle_model(w)
+    R = 6
+    ref, got = [], []
+    for seed in range(R):
+        r = oracle.smc_run(model, ev, 256, 0.5, 2, 5, 2, 0.5, key=90 + seed)
+        g = ctx.smc_run(256, 0.5, 2, 5, 2, 0.5, key=90 + seed, precision="fp64")
+        assert g[3][0]["beta"] == pytest.approx(r[3][0]["beta"], rel=1e-11)
+        ref.append(r[0])
+        got.append(g[0])
+    assert abs(np.mean(got) - np.mean(ref)) <= 2.0 * math.sqrt(_se(got) ** 2 + _se(ref) ** 2), (got, ref)
