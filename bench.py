@@ -40,11 +40,18 @@ UNIT = "evals/s"
 # split: FP32 phase, 8 split products per bin (~13.5 FLOP each) shared by 3
 #        detectors + ~15 FLOP per detector -> 51 FLOP, total 96 FP32 FLOP.
 # fp64: phase as mixed, carrier by sincospi (~30 FMA) and moments in FP64.
-WORK = {
-    "mixed": {"pipe": "fp64", "flop": 2.0 * (8.0 / 3.0 + 1.0), "fp32_flop": 45.0},
-    "split": {"pipe": "fp32", "flop": 96.0, "fp32_flop": 96.0},
-    "fp64": {"pipe": "fp64", "flop": 2.0 * (8.0 / 3.0 + 1.0) + 60.0 + 45.0, "fp32_flop": 0.0},
-}
+def work(precision, n_det=3):
+    """Algorithmic FLOP per active (bin, detector) of the gradient sweep with n_det detectors."""
+    phase64 = 2.0 * (8.0 / n_det + 1.0)          # FP64 FMA: 8 per bin shared by the detectors + 1 per detector
+    phase32 = 8.0 * 13.5 / n_det + 15.0          # split FP32 phase: 8 split products per bin + per-detector part
+    if precision == "mixed":
+        return {"pipe": "fp64", "flop": phase64, "fp32_flop": 45.0}
+    if precision == "split":
+        return {"pipe": "fp32", "flop": phase32 + 45.0, "fp32_flop": phase32 + 45.0}
+    return {"pipe": "fp64", "flop": phase64 + 60.0 + 45.0, "fp32_flop": 0.0}
+
+
+WORK = {p: work(p) for p in ("mixed", "split", "fp64")}
 
 
 # DRAM bytes (read + write) of one NUTS launch of this workload from an ncu
@@ -127,21 +134,35 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _oracle_sample(n_particles, seed):
+def _workload(name):
+    from paper_2601_02336_gb300 import inputs
+    return inputs.WORKLOADS[name]()
+
+
+def _describe(w):
+    metric = {0: "identity metric", 1: "covariance metric", 2: "per-particle local metric"}[w.metric]
+    det = "1 detector (F+ = 1)" if w.fixed_response else f"{w.n_det} detectors"
+    return (f"{w.name}: {w.n_dim}-D TaylorF2, {det}, {1.0 / w.df:g} s at 1/{1.0 / w.df:g} Hz "
+            f"({w.n_bins} bins, {w.f_min:g}-{w.f_max:g} Hz), {w.n_particles} particles, NUTS depth {w.max_depth}, "
+            f"alpha {w.alpha}, {w.n_mut} transitions/stage, {metric}; one step = one full SMC run")
+
+
+def _oracle_sample(n_particles, seed, name="bbh11", max_depth=None):
     """A bounded sample of the workload for the oracle: one NUTS transition of
     n_particles particles of the same event at beta = 0.5 (mid-run state)."""
     import oracle
     from paper_2601_02336_gb300 import inputs
     from tests import helpers
-    w = inputs.bbh11()
+    w = _workload(name)
     ev, th_inj, _ = helpers.make_event(w, seed=0)
     model = helpers.oracle_model(w)
     th = inputs.ball(w, th_inj, n_particles, 500 + seed, rel=1e-3)
     lnl, g = oracle.loglike(model, ev, th)
     sig = np.std(th, axis=0)
     eps = 0.5 * float(np.min(sig))
+    depth = w.max_depth if max_depth is None else max_depth
     t0 = time.perf_counter()
-    _, _, _, st = oracle.nuts_mutate(model, ev, 0.5, th, lnl, g, None, eps, w.max_depth, 1, key=77 + seed, ctr=1)
+    _, _, _, st = oracle.nuts_mutate(model, ev, 0.5, th, lnl, g, None, eps, depth, 1, key=77 + seed, ctr=1)
     dt = time.perf_counter() - t0
     return int(st["n_leapfrog"].sum()), dt
 
@@ -226,7 +247,7 @@ def main_loglike(args):
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
-            wk = WORK[prec]
+            wk = work(prec, w.n_det)
             tfl = n * act * wk["flop"] / (ms * 1e-3) / 1e12
             peak = peaks[1] if wk["pipe"] == "fp64" else peaks[0]
             row[prec] = {"evals_per_s": n / (ms * 1e-3), "ms_per_call": ms, "pipe": wk["pipe"],
@@ -284,6 +305,8 @@ def main_batch(args):
     w0 = ws[0]
     b = api.Batch(ctxs, [w.n_particles for w in ws], w0.alpha, w0.n_mut, w0.max_depth, w0.metric, w0.eps_scale,
                   precision=args.precision, max_stages=500)
+    if args.slots:
+        b.slots = args.slots
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for i in range(args.warmup):
         b.run([multirank.run_key(10_000 + 100 * i, rank, e) for e in range(len(ws))])
@@ -347,6 +370,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="bbh11", choices=["tiny", "bbh11", "bbh11_long", "bns", "batch64"])
     ap.add_argument("--mode", default="smc", choices=["smc", "loglike"])
+    ap.add_argument("--slots", type=int, default=0, choices=[0, 8, 16, 32],
+                    help="batch64: NUTS particles per CTA (0: autotuned)")
     ap.add_argument("--metric", type=int, default=None, choices=[0, 1, 2],
                     help="NUTS metric (default: the workload's): 0 identity, 1 covariance, 2 per-particle local")
     args = ap.parse_args()
@@ -379,7 +404,7 @@ def main():
     def allsum(x):
         return multirank.reduce_scalar(x, "sum", world, device="cuda")
 
-    w = inputs.bbh11()
+    w = inputs.WORKLOADS[args.workload]()
     if args.metric is not None:
         w.metric = args.metric
     ctx, th_inj, data = api.make_event(w, seed=multirank.event_seed(rank), device=local)
@@ -429,14 +454,15 @@ def main():
     peaks = (C.c_double * 3)()
     lib().sharpy_probe_peaks(local, peaks)
     fp32_peak, fp64_peak = peaks[0], peaks[1]
-    wk = WORK[args.precision]
+    wk = work(args.precision, w.n_det)
     secs = nuts_ms * 1e-3
     ach = bins * wk["flop"] / secs / 1e12
     peak = fp64_peak if wk["pipe"] == "fp64" else fp32_peak
     fp32_ach = bins * wk["fp32_flop"] / secs / 1e12
     kname = {"mixed": "MIXED", "split": "MIXED_SPLIT", "fp64": "FP64"}[args.precision]
-    roofline = {"bound": "alu", "kernel": f"nuts_kernel<{kname},3>", "achieved": ach, "peak": peak,
-                "unit": "TFLOP/s", "frac": ach / peak if peak else None, "traffic": _traffic(args.precision),
+    roofline = {"bound": "alu", "kernel": f"nuts_kernel<{kname},{w.n_det}>", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak if peak else None,
+                "traffic": _traffic(args.precision) if w.name == "bbh11" else None,
                 "traffic_unit": "bytes per NUTS launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "pipe": wk["pipe"], "flop_per_active_bin_det": wk["flop"],
                 "peak_source": f"measured {wk['pipe'].upper()} FMA probe on this GPU (sharpy_probe_peaks)",
@@ -500,11 +526,14 @@ def main():
         import oracle
         oracle.build()
         cores = os.cpu_count()
-        n_part = 8 * cores
-        e, dt = _oracle_sample(n_part, 0)
+        # about 10-30 s of oracle work: fewer particles and a shallower tree on the long segments
+        big = w.n_bins * w.n_det > 200_000
+        n_part = cores if big else 8 * cores
+        depth = 3 if big else w.max_depth
+        e, dt = _oracle_sample(n_part, 0, w.name, depth)
         cpu = {"value": e / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"oracle NUTS, one transition of {n_part} particles at beta=0.5 near the injection "
-                         f"of the same workload ({e} gradient evaluations, {dt:.1f} s)"}
+               "sample": f"oracle NUTS, one transition (depth {depth}) of {n_part} particles at beta=0.5 near the "
+                         f"injection of the same workload ({e} gradient evaluations, {dt:.1f} s)"}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -512,12 +541,7 @@ def main():
                "scaling": "weak", "vs_baseline": None,
                "dtype": {"mixed": "f32+f64", "split": "f32 (f64 per particle)", "fp64": "f64"}[args.precision],
                "data": "synthetic",
-               "config": {"workload": "bbh11: 11-D aligned-spin TaylorF2, 3 detectors, 8 s at 1/8 Hz "
-                                      "(8033 bins, 20-1024 Hz), 2048 particles, NUTS depth 6, alpha 0.5, "
-                                      "2 transitions/stage, "
-                                      + {0: "identity metric", 1: "covariance metric",
-                                         2: "per-particle local metric"}[w.metric]
-                                      + "; one step = one full SMC run",
+               "config": {"workload": _describe(w),
                           "precision": args.precision, "l2": "flushed (256 MB write) between steps",
                           "parallelism": f"one independent event per GPU x {world}",
                           "stages_per_run": n_stages},

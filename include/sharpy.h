@@ -295,9 +295,14 @@ int sharpy_batch_particles(sharpy_batch* b, int e, double* theta, double* lnl, s
    *n = stages written). nuts_ms and reweight_ms are 0. Synchronous. */
 int sharpy_batch_stages(sharpy_batch* b, int e, sharpy_stage* stages, int cap, int* n);
 /* Slot count (particles per NUTS CTA: 8, 16 or 32) the batch's launches
-   use, picked by timing each candidate on the batch's own first stage (0
-   before the first run). The results do not depend on it. */
+   use, picked by timing each candidate on full mutations of copies of the
+   particles at the third stage round of the first run (0 until then; the
+   launches use a count derived from the CTA count meanwhile). The results do
+   not depend on it. */
 int sharpy_batch_slots(sharpy_batch* b);
+/* Set the slot count (8, 16 or 32) instead of tuning it; 0 tunes it again on
+   the next run. SHARPY_EINVAL for other values. */
+int sharpy_batch_set_slots(sharpy_batch* b, int slots);
 
 /* Per-particle mass matrices (Sec. 5, "Exploitation of local geometry": at the
    start of each SMC iteration every particle gets the Hessian of the tempered

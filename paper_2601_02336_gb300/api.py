@@ -296,6 +296,10 @@ class Batch:
     def slots(self):
         return lib().sharpy_batch_slots(self._h)
 
+    @slots.setter
+    def slots(self, value):
+        check(lib().sharpy_batch_set_slots(self._h, int(value)), "sharpy_batch_set_slots")
+
 
 def recycle(theta, lnl, betas, lnz_t, key):
     """Sample recycling (sharpy_recycle): importance weights of a pool drawn from

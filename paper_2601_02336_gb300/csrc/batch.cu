@@ -11,6 +11,8 @@
 //
 // The NUTS slot count (particles per CTA) is picked by the autotuner
 // (tune.cuh) on the batch's own first stage; the results do not depend on it.
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -29,6 +31,7 @@ int enqueue_local_metric(sharpy_ctx* c, int64_t n, const double* theta, const do
 
 constexpr int kBatchRec = 9;  // beta, ess, dlnz, eps, accept, depth, leapfrogs, divergent, active bins
 constexpr int kRoundsPerCheck = 4;
+constexpr int kTuneRound = 3;  // the first run tunes the slot count on this round (full mutations on copies)
 
 // Start of a run: beta = 0, active, no stages, ln Z = 0, nothing done.
 __global__ void batch_init_kernel(int ne, double* beta, int* active, int* stage, double* lnz, double* tot,
@@ -380,7 +383,7 @@ int sharpy_batch_create(sharpy_batch** out, sharpy_ctx* const* events, int n_eve
     T.theta = A.th0;
     T.lnl = A.l0;
     T.grad = A.g0;
-    T.n_steps = 1;
+    T.n_steps = o->n_mut;
   }
   for (int i = 0; i < kNumSlotChoices; ++i)
     if (cudaMemcpy(b->d_map[i], maps[i].data(), maps[i].size() * sizeof(int2), cudaMemcpyHostToDevice) !=
@@ -396,12 +399,22 @@ void sharpy_batch_destroy(sharpy_batch* b) { batch_free(b); }
 
 int sharpy_batch_slots(sharpy_batch* b) { return b ? b->slots : 0; }
 
+int sharpy_batch_set_slots(sharpy_batch* b, int slots) {
+  if (!b || (slots != 0 && slots != 8 && slots != 16 && slots != 32)) return SHARPY_EINVAL;
+  b->slots = slots;
+  return SHARPY_OK;
+}
+
 int sharpy_batch_run(sharpy_batch* b, const uint64_t* keys, sharpy_batch_result* results, int* rounds,
                      sharpy_stream stream) {
   if (!b || !keys || !results) return SHARPY_EINVAL;
   SHARPY_CUDA_TRY(cudaSetDevice(b->device));
   cudaStream_t s = (cudaStream_t)stream;
   const int E = b->ne;
+  nvtxRangePushA("sharpy_batch_run");
+  struct RangeEnd {
+    ~RangeEnd() { nvtxRangePop(); }
+  } range_end;
   for (int e = 0; e < E; ++e) {
     b->h_stage[e].key = keys[e];
     b->h_nuts[e].key = keys[e];
@@ -421,23 +434,41 @@ int sharpy_batch_run(sharpy_batch* b, const uint64_t* keys, sharpy_batch_result*
     if (!rc) rc = sharpy_loglike_grad(c, b->n[e], th, b->ll + b->off[e], b->gr + b->doff[e], b->opt.precision, stream);
   }
   if (rc) return rc;
-  // round 1 runs eagerly; the first run also tunes the slot count on it
-  int nr = 1;
-  if ((rc = enqueue_round_stage(b, s))) return rc;
-  if (!b->slots) {
-    TuneCandidate cands[kNumSlotChoices];
-    auto trial = [&](int slots, cudaStream_t ts) -> int {
-      SHARPY_CUDA_TRY(cudaMemcpyAsync(b->th0, b->th, b->nd_total * sizeof(double), cudaMemcpyDeviceToDevice, ts));
-      SHARPY_CUDA_TRY(cudaMemcpyAsync(b->g0, b->gr, b->nd_total * sizeof(double), cudaMemcpyDeviceToDevice, ts));
-      SHARPY_CUDA_TRY(cudaMemcpyAsync(b->l0, b->ll, b->n_total * sizeof(double), cudaMemcpyDeviceToDevice, ts));
-      return enqueue_round_nuts(b, b->d_trial, slots, ts);
-    };
-    for (int i = 0; i < kNumSlotChoices; ++i) cands[i].slots = kSlotChoices[i];
-    if ((rc = tune_slots(cands, kNumSlotChoices, trial, s, &b->slots))) return rc;
+  // The first rounds run eagerly. Until the batch is tuned, the slot count
+  // comes from the CTA count (about two 32-slot CTAs per SM, else 16, else 8)
+  // and round kTuneRound times each candidate on full mutations of copies of
+  // the particles (the state of a mid-run stage, not the first one, whose
+  // trees all reach the depth limit).
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  const int guess = b->n_cta[slot_index(32)] >= 2u * (unsigned)sms ? 32
+                    : b->n_cta[slot_index(16)] >= 2u * (unsigned)sms ? 16 : 8;
+  const int eager = b->slots ? 1 : kTuneRound;
+  int nr = 0;
+  for (int r = 1; r <= eager; ++r) {
+    if ((rc = enqueue_round_stage(b, s))) return rc;
+    if (r == kTuneRound && !b->slots) {
+      SHARPY_CUDA_TRY(cudaMemcpyAsync(b->h_flags, b->flags, 2 * E * sizeof(int), cudaMemcpyDeviceToHost, s));
+      SHARPY_CUDA_TRY(cudaStreamSynchronize(s));
+      bool running = false;
+      for (int e = 0; e < E; ++e) running = running || (b->h_flags[e] && !b->h_flags[E + e]);
+      if (running) {
+        TuneCandidate cands[kNumSlotChoices];
+        auto trial = [&](int slots, cudaStream_t ts) -> int {
+          SHARPY_CUDA_TRY(cudaMemcpyAsync(b->th0, b->th, b->nd_total * sizeof(double), cudaMemcpyDeviceToDevice, ts));
+          SHARPY_CUDA_TRY(cudaMemcpyAsync(b->g0, b->gr, b->nd_total * sizeof(double), cudaMemcpyDeviceToDevice, ts));
+          SHARPY_CUDA_TRY(cudaMemcpyAsync(b->l0, b->ll, b->n_total * sizeof(double), cudaMemcpyDeviceToDevice, ts));
+          return enqueue_round_nuts(b, b->d_trial, slots, ts);
+        };
+        for (int i = 0; i < kNumSlotChoices; ++i) cands[i].slots = kSlotChoices[i];
+        if ((rc = tune_slots(cands, kNumSlotChoices, trial, s, &b->slots))) return rc;
+      }
+    }
+    if ((rc = enqueue_round_nuts(b, b->d_nuts, b->slots ? b->slots : guess, s))) return rc;
+    if ((rc = enqueue_round_record(b, s))) return rc;
+    ++nr;
   }
-  if ((rc = enqueue_round_nuts(b, b->d_nuts, b->slots, s))) return rc;
-  if ((rc = enqueue_round_record(b, s))) return rc;
-  if ((rc = capture_round(b, b->slots))) return rc;
+  if ((rc = capture_round(b, b->slots ? b->slots : guess))) return rc;
   for (;;) {
     SHARPY_CUDA_TRY(cudaMemcpyAsync(b->h_flags, b->flags, 2 * E * sizeof(int), cudaMemcpyDeviceToHost, s));
     SHARPY_CUDA_TRY(cudaStreamSynchronize(s));

@@ -2,6 +2,8 @@
 // per-stage state (beta, ln Z, particles, metric) kept on the device.
 #include <cmath>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "context.cuh"
 #include "tune.cuh"
 
@@ -20,6 +22,9 @@ int enqueue_local_metric(sharpy_ctx* c, int64_t n, const double* theta, const do
 
 // Per-stage record: [beta, ess, dlnz, eps, accept_sum, depth_sum, n_leapfrog, n_divergent, active_bins]
 constexpr int kRec = 9;
+// Stage on which a context without a tuned slot count times the candidates
+// (a mid-run state; on the first stage every tree reaches the depth limit).
+constexpr int kTuneStage = 3;
 
 __global__ void stage_record_kernel(int64_t n, int D, const sharpy_nuts_stats* __restrict__ st,
                                     const double* beta, const double* ess, const double* dlnz, const double* cov,
@@ -112,8 +117,16 @@ extern "C" int sharpy_smc_run(sharpy_ctx* c, const sharpy_smc_options* o, uint64
     return fail(SHARPY_ECUDA);
   double beta = 0.0;
   int t = 0;
+  nvtxRangePushA("sharpy_smc_run");
+  struct RangeEnd {
+    ~RangeEnd() { nvtxRangePop(); }
+  } range_end;
   while (beta < 1.0 && t < o->max_stages) {
     ++t;
+    nvtxRangePushA("stage");
+    struct StageEnd {
+      ~StageEnd() { nvtxRangePop(); }
+    } stage_end;
     double u0, u1;
     uniform2(key, 0u, (uint32_t)t, RNG_RESAMPLE, 0u, &u0, &u1);
     if (o->timing) cudaEventRecord(evr, s);
@@ -125,13 +138,14 @@ extern "C" int sharpy_smc_run(sharpy_ctx* c, const sharpy_smc_options* o, uint64
     if (local && (rc = enqueue_local_metric(c, n, th, beta_state, 0.0, nullptr, pminv, pchol, s))) return fail(rc);
     const double* pm = local ? pminv : nullptr;
     const double* pc = local ? pchol : nullptr;
-    if (t == 1 && tune) {
-      // pick the slot count on this stage: one transition on copies of the particles
+    if (t == kTuneStage && tune) {
+      // pick the slot count on this stage: its full mutation on copies of the particles
       auto go = [&](int slots, cudaStream_t ts) -> int {
         SHARPY_CUDA_TRY(cudaMemcpyAsync(trial, th, (size_t)n * (2 * D + 1) * sizeof(double),
                                         cudaMemcpyDeviceToDevice, ts));
         return enqueue_nuts(c, n, beta_state, 0.0, trial, trial + 2 * n * D, trial + n * D, minv, cov_step,
-                            o->eps_scale, o->max_depth, 1, key, (uint32_t)t << 8, o->precision, st, ts, slots, pm,
+                            o->eps_scale, o->max_depth, o->n_mut, key, (uint32_t)t << 8, o->precision, st, ts,
+                            slots, pm,
                             pc);
       };
       TuneCandidate cands[kNumSlotChoices];

@@ -167,18 +167,24 @@ __device__ void sweep_mixed(const DevEvent& ev, const SweepCoef& sc, float* mom)
       f = __ldg(ev.b64 + (int64_t)8 * K + k);
     } else {
       // sum_j alpha_j B_j mod 1: p = ahi*bhi is exact up to e (FMA), its integer
-      // part is removed exactly, the fraction accumulates in F (kept in
-      // [-1/2, 1/2]), the error and cross terms in Sm.
-      F = sc.c0f;
+      // part is removed exactly; the fractions are summed pairwise, reduced to
+      // [-1/2, 1/2] at every level (three levels instead of an eight-step
+      // chain), the error and cross terms likewise pairwise in Sm.
+      static_assert(kNPn == 8, "the pairwise tree below is written for eight basis terms");
+      float fr[kNPn], er[kNPn];
 #pragma unroll
       for (int j = 0; j < kNPn; ++j) {
         const float bl = __ldg(ev.b32lo + (int64_t)j * K + k);
         const float p = __fmul_rn(ah[j], bf[j]);
-        Sm += fmaf(ah[j], bf[j], -p);
-        Sm = fmaf(ah[j], bl, fmaf(alo[j], bf[j], Sm));
-        F = __fadd_rn(F, frac_turn(p));
-        if (j & 1) F = frac_turn(F);
+        fr[j] = frac_turn(p);
+        er[j] = fmaf(ah[j], bl, fmaf(alo[j], bf[j], fmaf(ah[j], bf[j], -p)));
       }
+      const float f01 = frac_turn(__fadd_rn(fr[0], fr[1])), f23 = frac_turn(__fadd_rn(fr[2], fr[3]));
+      const float f45 = frac_turn(__fadd_rn(fr[4], fr[5])), f67 = frac_turn(__fadd_rn(fr[6], fr[7]));
+      const float f03 = frac_turn(__fadd_rn(f01, f23)), f47 = frac_turn(__fadd_rn(f45, f67));
+      F = frac_turn(__fadd_rn(__fadd_rn(f03, f47), sc.c0f));
+      Sm = __fadd_rn(__fadd_rn(__fadd_rn(er[0], er[1]), __fadd_rn(er[2], er[3])),
+                     __fadd_rn(__fadd_rn(er[4], er[5]), __fadd_rn(er[6], er[7])));
     }
 #pragma unroll
     for (int a = 0; a < NDET; ++a) {

@@ -46,7 +46,7 @@ def test_batch_matches_separate_runs(precision):
     kw = dict(alpha=0.5, n_mut=2, max_depth=6, metric=0, eps_scale=0.5, precision=precision, max_stages=200)
     b = api.Batch(ctxs, [w.n_particles for w in ws], **kw)
     res, rounds = b.run(keys)
-    assert b.slots in (8, 16, 32)
+    assert b.slots in (0, 8, 16, 32)  # 0: every event finished before the tuning round
     assert rounds >= max(r["n_stages"] for r in res)
     _check_against_runs(b, ws, ctxs, keys, res, **kw)
     # a second run replays the cached graph without tuning and repeats itself
