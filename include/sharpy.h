@@ -338,6 +338,14 @@ int sharpy_recycle(int64_t m, int d, int t, const double* theta, const double* l
                    const double* lnz_t, uint64_t key, double* log_w, double* out_theta, int64_t* n_out,
                    sharpy_stream stream);
 
+/* The kernels' random numbers on the host: the two 53-bit uniforms u[2] of
+   Philox4x32-10 (Salmon et al. 2011) under `key` at counter (c0, c1, c2, c3).
+   The run uses (particle, step, purpose, index) counters with purposes 1
+   prior, 2 momentum, 3 direction, 4 leaf, 5 top-level acceptance, 6
+   resampling (particle 0, step = stage), 7 recycling. Lets a host-side stage
+   loop reproduce sharpy_smc_run (e.g. to checkpoint between stages). */
+void sharpy_uniform2(uint64_t key, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, double* u);
+
 /* Measurement helper: FP32 FMA TFLOP/s, FP64 FMA TFLOP/s and SFU sin+cos
    Gop/s of `device` from register-only kernels (out[3], host). Used as the
    roofline denominators of the ALU-bound likelihood sweep. Synchronous. */

@@ -95,6 +95,8 @@ _SIGS = {
     "sharpy_local_metric": (C.c_int, [_CTX, C.c_int64, _VP, C.c_double, _VP, _VP, _VP, _VP]),
     "sharpy_recycle": (C.c_int, [C.c_int64, C.c_int, C.c_int, _VP, _VP, C.POINTER(C.c_double),
                                  C.POINTER(C.c_double), C.c_uint64, _VP, _VP, C.POINTER(C.c_int64), _VP]),
+    "sharpy_uniform2": (None, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
+                                C.POINTER(C.c_double)]),
     "sharpy_get_status": (C.c_int, [_CTX]),
     "sharpy_clear_status": (C.c_int, [_CTX]),
     "sharpy_error_string": (C.c_char_p, [C.c_int]),

@@ -236,6 +236,99 @@ class Context:
         check(lib().sharpy_clear_status(self._h), "sharpy_clear_status")
 
 
+def uniform2(key, c0, c1, c2, c3):
+    """The kernels' Philox4x32-10 uniforms at one counter (sharpy_uniform2)."""
+    u = (C.c_double * 2)()
+    lib().sharpy_uniform2(key, c0, c1, c2, c3, u)
+    return u[0], u[1]
+
+
+class SMCRunner:
+    """The SMC loop of sharpy_smc_run driven stage by stage from the host through
+    the public calls (reweight/resample, local metric, NUTS), with checkpoints
+    at stage boundaries. It draws the same random numbers as sharpy_smc_run, so
+    a run matches sharpy_smc_run with the same key bit for bit, and a run
+    restored from a checkpoint continues exactly as the uninterrupted one."""
+
+    RESAMPLE = 6        # Philox purpose of the resampling uniform
+    STAGE_COUNTER = 256  # NUTS step counters of stage t start at t * 256
+
+    def __init__(self, ctx, n_particles, alpha, n_mut, max_depth, metric, eps_scale, key, precision="mixed",
+                 max_stages=500):
+        self.ctx = ctx
+        self.opts = dict(n_particles=int(n_particles), alpha=float(alpha), n_mut=int(n_mut),
+                         max_depth=int(max_depth), metric=int(metric), eps_scale=float(eps_scale), key=int(key),
+                         precision=precision, max_stages=int(max_stages))
+        self.theta = self.lnl = self.grad = None
+        self.beta, self.lnz, self.stage = 0.0, 0.0, 0
+        self.records = []
+
+    def start(self):
+        o = self.opts
+        self.theta = self.ctx.prior_sample(o["n_particles"], o["key"], 0)
+        self.lnl, self.grad = self.ctx.loglike_grad(self.theta, o["precision"])
+        self.beta, self.lnz, self.stage, self.records = 0.0, 0.0, 0, []
+        return self
+
+    @property
+    def done(self):
+        return self.beta >= 1.0 or self.stage >= self.opts["max_stages"]
+
+    def step(self):
+        """One stage: reweight, resample, metric, n_mut NUTS transitions."""
+        o = self.opts
+        self.stage += 1
+        t = self.stage
+        u = uniform2(o["key"], 0, t, self.RESAMPLE, 0)[0]
+        r = self.ctx.reweight_resample(self.theta, self.lnl, self.grad, self.beta, o["alpha"], u)
+        beta_next, dlnz = float(r["beta_next"]), float(r["dlnz"])
+        args = (o["max_depth"], o["n_mut"], o["key"], t * self.STAGE_COUNTER)
+        if o["metric"] == 2:
+            met = self.ctx.local_metric(self.theta, beta_next, want=("inv_mass", "chol"))
+            st = self.ctx.nuts_mutate_local(beta_next, self.theta, self.lnl, self.grad, met["inv_mass"], met["chol"],
+                                            o["eps_scale"], *args, precision=o["precision"])
+        elif o["metric"] == 1:
+            st = self.ctx.nuts_mutate(beta_next, self.theta, self.lnl, self.grad, r["cov"], o["eps_scale"], *args,
+                                      precision=o["precision"])
+        else:
+            eps = o["eps_scale"] * float(np.sqrt(np.diag(r["cov"].cpu().numpy())).min())
+            st = self.ctx.nuts_mutate(beta_next, self.theta, self.lnl, self.grad, None, eps, *args,
+                                      precision=o["precision"])
+        s = Context.stats_to_numpy(st)
+        self.records.append({"beta": beta_next, "dlnz": dlnz, "ess": float(r["ess"]),
+                             "n_leapfrog": int(s["n_leapfrog"].sum())})
+        self.beta = beta_next
+        self.lnz += dlnz
+        return self
+
+    def run(self):
+        if self.theta is None:
+            self.start()
+        while not self.done:
+            self.step()
+        return self.lnz
+
+    def save(self, path):
+        """Checkpoint at a stage boundary (.npz)."""
+        np.savez(path, theta=self.theta.cpu().numpy(), lnl=self.lnl.cpu().numpy(), grad=self.grad.cpu().numpy(),
+                 scalars=np.array([self.beta, self.lnz, self.stage], dtype=np.float64),
+                 opts=np.array(repr(self.opts)), records=np.array(repr(self.records)))
+
+    @classmethod
+    def load(cls, ctx, path):
+        import ast
+        z = np.load(path, allow_pickle=False)
+        r = cls(ctx, **ast.literal_eval(str(z["opts"])))
+        dev = f"cuda:{ctx.device}"
+        r.theta = torch.tensor(z["theta"], dtype=torch.float64, device=dev)
+        r.lnl = torch.tensor(z["lnl"], dtype=torch.float64, device=dev)
+        r.grad = torch.tensor(z["grad"], dtype=torch.float64, device=dev)
+        beta, lnz, stage = (float(x) for x in z["scalars"])
+        r.beta, r.lnz, r.stage = beta, lnz, int(stage)
+        r.records = ast.literal_eval(str(z["records"]))
+        return r
+
+
 class Batch:
     """Many events sampled together (sharpy_batch_*): one persistent NUTS launch
     and one reweight launch per stage round cover every event still tempering;

@@ -171,6 +171,7 @@ int enqueue_round_nuts(sharpy_batch* b, const NutsArgs* args, int slots, cudaStr
   NutsArgs P{};
   P.batch = args;
   P.cta_map = b->d_map[i];
+  P.local_metric = b->opt.metric == 2 ? 1 : 0;
   return launch_nuts(b->opt.precision, b->ndet, slots, P, b->n_cta[i], s);
 }
 
@@ -370,6 +371,7 @@ int sharpy_batch_create(sharpy_batch** out, sharpy_ctx* const* events, int n_eve
     U.cov_step = o->metric == 0 ? A.cov : nullptr;
     U.pminv = o->metric == 2 ? b->pminv + b->moff[e] : nullptr;
     U.pchol = o->metric == 2 ? b->pchol + b->moff[e] : nullptr;
+    U.local_metric = o->metric == 2 ? 1 : 0;
     U.step = o->eps_scale;
     U.max_depth = o->max_depth;
     U.n_steps = o->n_mut;

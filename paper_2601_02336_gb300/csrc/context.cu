@@ -305,3 +305,7 @@ const char* sharpy_error_string(int code) {
 }
 
 }  // extern "C"
+
+extern "C" void sharpy_uniform2(uint64_t key, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, double* u) {
+  if (u) sharpy::uniform2(key, c0, c1, c2, c3, u, u + 1);
+}

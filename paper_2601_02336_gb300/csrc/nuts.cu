@@ -66,6 +66,7 @@ int enqueue_nuts(sharpy_ctx* c, int64_t n, const double* beta_ptr, double beta, 
   const int nd = c->model.model == SHARPY_MODEL_TAYLORF2 ? c->ev.n_det : 1;
   A.pminv = pminv;
   A.pchol = pchol;
+  A.local_metric = pminv ? 1 : 0;
   A.batch = nullptr;
   A.cta_map = nullptr;
   A.active = nullptr;

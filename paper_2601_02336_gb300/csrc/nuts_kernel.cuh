@@ -68,6 +68,7 @@ struct NutsArgs {
   const double* minv;      // [D][D] or null
   const double* pminv;     // [n][D][D] per-particle metric (with pchol), or null
   const double* pchol;
+  int local_metric;        // 1: per-particle metric (pminv, pchol); sizes the shared memory
   const double* cov_step;  // identity metric with step = eps_scale * min sqrt(diag cov)
   double step;
   int max_depth;
@@ -91,8 +92,12 @@ template <int SLOTS, class VT>
 struct NutsShared {
   double pos[P_COUNT][kMaxDim][SLOTS];
   VT vec[F_COUNT][kMaxDim][SLOTS];
-  VT minv[kMaxDim][kMaxDim][SLOTS];  // each slot's metric (a copy of the shared one, or its own)
-  VT chol[kMaxDim][kMaxDim][SLOTS];
+  // metric: minv and its Cholesky factor, [kMaxDim][kMaxDim][mstride] each, after
+  // NutsSmem in dynamic shared memory: one copy (shared metric, mstride = 1) or
+  // one per slot (per-particle metric, mstride = SLOTS)
+  VT* mmin;
+  VT* mchol;
+  int mstride;
   long long lokey[kMaxDim], hikey[kMaxDim];  // order keys of the prior box (see okey)
   double eps, beta;
   double lp_const;  // sum of the prior's constant log terms
@@ -171,8 +176,8 @@ struct Nuts {
   int D;
   __device__ Nuts(const NutsArgs& a, NutsShared<SLOTS, VT>& sh, int slot) : A(a), S(sh), s(slot), D(a.m.n_dim) {}
   __device__ VT& V(int f, int d) { return S.vec[f][d][s]; }
-  __device__ VT& MI(int i, int j) { return S.minv[i][j][s]; }
-  __device__ VT& CH(int i, int j) { return S.chol[i][j][s]; }
+  __device__ VT& MI(int i, int j) { return S.mmin[(i * kMaxDim + j) * S.mstride + (S.mstride > 1 ? s : 0)]; }
+  __device__ VT& CH(int i, int j) { return S.mchol[(i * kMaxDim + j) * S.mstride + (S.mstride > 1 ? s : 0)]; }
   __device__ double& X(int f, int d) { return S.pos[f][d][s]; }
 
   // v = Minv r for the momentum stored in field f
@@ -453,6 +458,20 @@ struct Nuts {
 };
 
 template <int PREC, int NDET, int SLOTS>
+struct NutsSmem;
+
+// Byte offset of the metric arrays in dynamic shared memory and the total size.
+template <int PREC, int NDET, int SLOTS>
+__host__ __device__ constexpr size_t nuts_metric_offset() {
+  return (sizeof(NutsSmem<PREC, NDET, SLOTS>) + 15) / 16 * 16;
+}
+template <int PREC, int NDET, int SLOTS>
+__host__ __device__ constexpr size_t nuts_smem_bytes(bool local) {
+  using VT = typename std::conditional<PREC == SHARPY_FP64, double, float>::type;
+  return nuts_metric_offset<PREC, NDET, SLOTS>() + 2 * kMaxDim * kMaxDim * (local ? SLOTS : 1) * sizeof(VT);
+}
+
+template <int PREC, int NDET, int SLOTS>
 struct NutsSmem {
   using DT = typename std::conditional<PREC == SHARPY_FP64, double, float>::type;
   using MT = typename MomType<PREC>::type;
@@ -501,6 +520,9 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(const __grid_c
 
   // metric, its Cholesky factor (diagonal fallback; computed in FP64), step size, beta
   if (threadIdx.x == 0) {
+    S.mstride = A.local_metric ? SLOTS : 1;
+    S.mmin = reinterpret_cast<VT*>(smem_raw + nuts_metric_offset<PREC, NDET, SLOTS>());
+    S.mchol = S.mmin + kMaxDim * kMaxDim * S.mstride;
     double mi[kMaxDim][kMaxDim], ch[kMaxDim][kMaxDim];
     for (int i = 0; i < D; ++i)
       for (int j = 0; j < D; ++j) mi[i][j] = A.minv ? A.minv[i * D + j] : (i == j ? 1.0 : 0.0);
@@ -532,8 +554,8 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(const __grid_c
       for (int j = 0; j < D; ++j) {
         if (i != j && mi[i][j] != 0.0) diag = false;
         if (mi[i][j] != (i == j ? 1.0 : 0.0)) ident = false;
-        S.minv[i][j][0] = (VT)mi[i][j];
-        S.chol[i][j][0] = (VT)ch[i][j];
+        S.mmin[i * kMaxDim + j] = (VT)mi[i][j];  // the one copy (or slot 0's)
+        S.mchol[i * kMaxDim + j] = (VT)ch[i][j];
       }
     S.metric_kind = A.pminv ? METRIC_DENSE : ident ? METRIC_IDENTITY : (diag ? METRIC_DIAGONAL : METRIC_DENSE);
     for (int i = 0; i < D; ++i) {
@@ -554,13 +576,6 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(const __grid_c
     }
     S.eps = eps;
     S.beta = A.beta_ptr ? *A.beta_ptr : A.beta;
-  }
-  __syncthreads();
-  // every slot starts from the shared metric (per-particle metrics replace it below)
-  for (int e = threadIdx.x; e < kMaxDim * kMaxDim * (SLOTS - 1); e += blockDim.x) {
-    const int ij = e / (SLOTS - 1), k = 1 + e % (SLOTS - 1);
-    S.minv[ij / kMaxDim][ij % kMaxDim][k] = S.minv[ij / kMaxDim][ij % kMaxDim][0];
-    S.chol[ij / kMaxDim][ij % kMaxDim][k] = S.chol[ij / kMaxDim][ij % kMaxDim][0];
   }
   __syncthreads();
 
@@ -711,9 +726,10 @@ int launch_nuts_impl(int slots, const NutsArgs& A, unsigned grid, cudaStream_t s
     kernel<<<g, kNutsWarps * 32, bytes, s>>>(A);
     return cudaGetLastError() == cudaSuccess ? SHARPY_OK : SHARPY_ECUDA;
   };
-  if (slots == 32) return go(nuts_kernel<P, ND, 32>, 32, sizeof(NutsSmem<P, ND, 32>));
-  if (slots == 16) return go(nuts_kernel<P, ND, 16>, 16, sizeof(NutsSmem<P, ND, 16>));
-  return go(nuts_kernel<P, ND, 8>, 8, sizeof(NutsSmem<P, ND, 8>));
+  const bool local = A.local_metric != 0;
+  if (slots == 32) return go(nuts_kernel<P, ND, 32>, 32, nuts_smem_bytes<P, ND, 32>(local));
+  if (slots == 16) return go(nuts_kernel<P, ND, 16>, 16, nuts_smem_bytes<P, ND, 16>(local));
+  return go(nuts_kernel<P, ND, 8>, 8, nuts_smem_bytes<P, ND, 8>(local));
 }
 
 }  // namespace sharpy
