@@ -58,8 +58,8 @@ WORK = {p: work(p) for p in ("mixed", "split", "fp64")}
 # capture (profiles/nuts_kernel_bbh11.md), valid only for the kernel sources
 # it was taken on: reported as roofline.traffic while their hash matches.
 TRAFFIC_SOURCES = ["nuts_kernel.cuh", "sweep.cuh", "physics.cuh", "common.cuh"]
-TRAFFIC = {"sources_sha256_16": "3d6e6d91dcf306d1",
-           "mixed": 1736192 + 1003264, "split": 1793536 + 1057280}
+TRAFFIC = {"sources_sha256_16": "80e1db162e883323",
+           "mixed": 1844224 + 1082112, "split": 1789952 + 1033728}
 
 
 def _traffic(precision):
@@ -314,7 +314,7 @@ def main_batch(args):
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
-    evals, bins, rounds, step_ms, lnzs = 0.0, 0.0, [], [], []
+    evals, bins, rounds, step_ms, lnzs, launches = 0.0, 0.0, [], [], [], 0
     for k in range(args.steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -326,6 +326,7 @@ def main_batch(args):
         evals += sum(r["n_leapfrog"] for r in res)
         bins += sum(r["active_bins"] for r in res)
         rounds.append(nr)
+        launches += b.launches
         lnzs.append([r["lnz"] for r in res])
     barrier()
     clk = clocks.stop()
@@ -349,7 +350,7 @@ def main_batch(args):
                "events_per_hour": n_ev / (t_max * 1e-3) * 3600.0,
                "round_ms": t_max / max(sum(rounds), 1),
                "achieved_tflops_whole_step": bins * wk["flop"] / (t_rank * 1e-3) / 1e12,
-               "gpu_launches": None, "clocks": clk,
+               "gpu_launches": launches, "clocks": clk,
                "lnz_first_events": [float(x) for x in lnzs[0][:4]]}
         print(json.dumps(out))
     if world > 1:
@@ -440,7 +441,9 @@ def main():
         bins += sum(r["active_bins"] for r in rec)
         nuts_ms += sum(r["nuts_ms"] for r in rec)
         rew_ms += sum(r["reweight_ms"] for r in rec)
-        launches += 2 + 5 * len(rec)
+        # prior draw and ln L, then per stage: reweight, covariance, systematic, save, gather, the
+        # local metric (metric 2), NUTS, record (the slot tuner ran in the warm-up runs)
+        launches += 2 + (7 + (1 if w.metric == 2 else 0)) * len(rec)
         lnzs.append(lnz)
         n_stages.append(len(rec))
     barrier()

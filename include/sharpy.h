@@ -303,6 +303,10 @@ int sharpy_batch_slots(sharpy_batch* b);
 /* Set the slot count (8, 16 or 32) instead of tuning it; 0 tunes it again on
    the next run. SHARPY_EINVAL for other values. */
 int sharpy_batch_set_slots(sharpy_batch* b, int slots);
+/* Kernels the last sharpy_batch_run launched: eager launches counted as they
+   are enqueued, every graph replay counted by the kernel nodes of the
+   captured round. -1 if b is NULL. */
+int64_t sharpy_batch_launches(sharpy_batch* b);
 
 /* Per-particle mass matrices (Sec. 5, "Exploitation of local geometry": at the
    start of each SMC iteration every particle gets the Hessian of the tempered

@@ -110,6 +110,9 @@ _SIGS = {
     "ref_nuts_mutate": (C.c_int, [_P(Model), _P(Event), C.c_int64, C.c_double, _D, _D, _D, _D,
                                   C.c_double, C.c_int, C.c_int, C.c_uint64, C.c_uint32,
                                   _P(NutsStats)]),
+    "ref_nuts_mutate_ids": (C.c_int, [_P(Model), _P(Event), C.c_int64, _P(C.c_int64), C.c_double, _D, _D, _D,
+                                      _D, C.c_double, C.c_int, C.c_int, C.c_uint64, C.c_uint32,
+                                      _P(NutsStats)]),
     "ref_smc_reweight": (C.c_int, [C.c_int64, _D, C.c_double, C.c_double, _D, _D, _D, _D]),
     "ref_systematic_resample": (C.c_int, [C.c_int64, _D, C.c_double, _P(C.c_int32)]),
     "ref_weighted_cov": (C.c_int, [C.c_int, C.c_int64, _D, _D, _D]),
@@ -274,7 +277,8 @@ def prior_logpdf_grad(model, theta):
     return lp, g
 
 
-def nuts_mutate(model, event, beta, theta, lnl, grad, inv_mass, step, max_depth, n_steps, key, ctr):
+def nuts_mutate(model, event, beta, theta, lnl, grad, inv_mass, step, max_depth, n_steps, key, ctr, ids=None):
+    """ids: the rows' indices in the ensemble (they name each particle's random numbers); default 0..N-1."""
     theta = _f64(theta).copy()
     lnl = _f64(lnl).copy()
     grad = _f64(grad).copy()
@@ -282,8 +286,15 @@ def nuts_mutate(model, event, beta, theta, lnl, grad, inv_mass, step, max_depth,
     st = (NutsStats * n)()
     im = _f64(inv_mass) if inv_mass is not None else None
     evp = C.byref(event.ev) if event is not None else None
-    _check(lib().ref_nuts_mutate(C.byref(model), evp, n, beta, _dp(theta), _dp(lnl), _dp(grad),
-                                 _dp(im), step, max_depth, n_steps, key, ctr, st), "nuts_mutate")
+    if ids is None:
+        _check(lib().ref_nuts_mutate(C.byref(model), evp, n, beta, _dp(theta), _dp(lnl), _dp(grad),
+                                     _dp(im), step, max_depth, n_steps, key, ctr, st), "nuts_mutate")
+    else:
+        idv = np.ascontiguousarray(ids, dtype=np.int64)
+        assert idv.shape == (n,)
+        _check(lib().ref_nuts_mutate_ids(C.byref(model), evp, n, idv.ctypes.data_as(C.POINTER(C.c_int64)), beta,
+                                         _dp(theta), _dp(lnl), _dp(grad), _dp(im), step, max_depth, n_steps, key,
+                                         ctr, st), "nuts_mutate")
     stats = {
         "accept_sum": np.array([s.accept_sum for s in st]),
         "depth_sum": np.array([s.depth_sum for s in st]),

@@ -177,6 +177,14 @@ int ref_nuts_mutate(const ref_model* m, const ref_event* ev, int64_t n, double b
                     double step, int max_depth, int n_steps, uint64_t key, uint32_t ctr,
                     ref_nuts_stats* stats);
 
+/* As ref_nuts_mutate on n rows of an ensemble: row i is the particle whose
+   index in the ensemble is ids[i] (0 <= ids[i] < 2^32), which names its
+   random numbers. */
+int ref_nuts_mutate_ids(const ref_model* m, const ref_event* ev, int64_t n, const int64_t* ids, double beta,
+                        double* theta, double* lnl, double* grad, const double* inv_mass,
+                        double step, int max_depth, int n_steps, uint64_t key, uint32_t ctr,
+                        ref_nuts_stats* stats);
+
 /* As ref_nuts_mutate with one inverse mass matrix per particle
    (inv_mass [N][D][D]: the local metric of Sec. 5). */
 int ref_nuts_mutate_local(const ref_model* m, const ref_event* ev, int64_t n, double beta,

@@ -253,10 +253,13 @@ using namespace oracle;
 
 extern "C" {
 
-int ref_nuts_mutate(const ref_model* m, const ref_event* ev, int64_t n, double beta, double* theta,
-                    double* lnl, double* grad, const double* inv_mass, double step, int max_depth,
-                    int n_steps, uint64_t key, uint32_t ctr, ref_nuts_stats* stats) {
+int ref_nuts_mutate_ids(const ref_model* m, const ref_event* ev, int64_t n, const int64_t* ids, double beta,
+                        double* theta, double* lnl, double* grad, const double* inv_mass, double step,
+                        int max_depth, int n_steps, uint64_t key, uint32_t ctr, ref_nuts_stats* stats) {
   if (max_depth < 0 || max_depth > kMaxDepth) return -1;
+  if (ids)
+    for (int64_t i = 0; i < n; ++i)
+      if (ids[i] < 0 || ids[i] > 0xffffffffLL) return -1;
   Sampler s;
   s.m = m;
   s.ev = ev;
@@ -266,12 +269,15 @@ int ref_nuts_mutate(const ref_model* m, const ref_event* ev, int64_t n, double b
   int D = s.D;
 #pragma omp parallel for schedule(dynamic, 1)
   for (int64_t i = 0; i < n; ++i) {
+    // the transition's random numbers are named by the particle's index in
+    // the ensemble, so any subset can be run on its own
+    const uint32_t pid = (uint32_t)(ids ? ids[i] : i);
     Point cur;
     for (int j = 0; j < D; ++j) cur.th[j] = theta[i * D + j];
     s.evaluate(cur);  // U and grad U at the current position (ln L recomputed: plain)
     ref_nuts_stats st = {0.0, 0, 0, 0};
     for (int t = 0; t < n_steps; ++t)
-      s.transition(cur, key, (uint32_t)i, ctr + (uint32_t)t, step, max_depth, &st);
+      s.transition(cur, key, pid, ctr + (uint32_t)t, step, max_depth, &st);
     for (int j = 0; j < D; ++j) {
       theta[i * D + j] = cur.th[j];
       grad[i * D + j] = cur.gl[j];
@@ -280,6 +286,13 @@ int ref_nuts_mutate(const ref_model* m, const ref_event* ev, int64_t n, double b
     if (stats) stats[i] = st;
   }
   return 0;
+}
+
+int ref_nuts_mutate(const ref_model* m, const ref_event* ev, int64_t n, double beta, double* theta,
+                    double* lnl, double* grad, const double* inv_mass, double step, int max_depth,
+                    int n_steps, uint64_t key, uint32_t ctr, ref_nuts_stats* stats) {
+  return ref_nuts_mutate_ids(m, ev, n, nullptr, beta, theta, lnl, grad, inv_mass, step, max_depth, n_steps, key,
+                             ctr, stats);
 }
 
 // As ref_nuts_mutate, each particle with its own inverse mass matrix

@@ -90,6 +90,7 @@ _SIGS = {
     "sharpy_batch_stages": (C.c_int, [_VP, C.c_int, C.POINTER(Stage), C.c_int, C.POINTER(C.c_int)]),
     "sharpy_batch_slots": (C.c_int, [_VP]),
     "sharpy_batch_set_slots": (C.c_int, [_VP, C.c_int]),
+    "sharpy_batch_launches": (C.c_int64, [_VP]),
     "sharpy_nuts_mutate_local": (C.c_int, [_CTX, C.c_int64, C.c_double, _VP, _VP, _VP, _VP, _VP, C.c_double,
                                            C.c_int, C.c_int, C.c_uint64, C.c_uint64, C.c_int, _VP, _VP]),
     "sharpy_local_metric": (C.c_int, [_CTX, C.c_int64, _VP, C.c_double, _VP, _VP, _VP, _VP]),

@@ -393,6 +393,11 @@ class Batch:
     def slots(self, value):
         check(lib().sharpy_batch_set_slots(self._h, int(value)), "sharpy_batch_set_slots")
 
+    @property
+    def launches(self):
+        """Kernels the last run launched (sharpy_batch_launches)."""
+        return int(lib().sharpy_batch_launches(self._h))
+
 
 def recycle(theta, lnl, betas, lnz_t, key):
     """Sample recycling (sharpy_recycle): importance weights of a pool drawn from

@@ -128,6 +128,8 @@ struct sharpy_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int graph_slots = 0;
+  int64_t graph_kernels = 0;  // kernel nodes of the captured round
+  int64_t launches = 0;       // kernels launched by the last run (graph replays count their nodes)
 };
 
 static void batch_free(sharpy_batch* b) {
@@ -203,6 +205,16 @@ int capture_round(sharpy_batch* b, int slots) {
   b->graph = g;
   SHARPY_CUDA_TRY(cudaGraphInstantiate(&b->exec, g, 0));
   b->graph_slots = slots;
+  size_t nn = 0;
+  SHARPY_CUDA_TRY(cudaGraphGetNodes(g, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (nn) SHARPY_CUDA_TRY(cudaGraphGetNodes(g, nodes.data(), &nn));
+  b->graph_kernels = 0;
+  for (size_t i = 0; i < nn; ++i) {
+    cudaGraphNodeType ty;
+    SHARPY_CUDA_TRY(cudaGraphNodeGetType(nodes[i], &ty));
+    if (ty == cudaGraphNodeTypeKernel) ++b->graph_kernels;
+  }
   return SHARPY_OK;
 }
 }  // namespace
@@ -401,6 +413,8 @@ void sharpy_batch_destroy(sharpy_batch* b) { batch_free(b); }
 
 int sharpy_batch_slots(sharpy_batch* b) { return b ? b->slots : 0; }
 
+int64_t sharpy_batch_launches(sharpy_batch* b) { return b ? b->launches : -1; }
+
 int sharpy_batch_set_slots(sharpy_batch* b, int slots) {
   if (!b || (slots != 0 && slots != 8 && slots != 16 && slots != 32)) return SHARPY_EINVAL;
   b->slots = slots;
@@ -428,6 +442,10 @@ int sharpy_batch_run(sharpy_batch* b, const uint64_t* keys, sharpy_batch_result*
   SHARPY_CUDA_TRY(cudaMemcpyAsync(b->d_trial, b->h_trial.data(), E * sizeof(NutsArgs), cudaMemcpyHostToDevice, s));
   batch_init_kernel<<<1, 256, 0, s>>>(E, b->beta, b->active, b->stage, b->lnz, b->tot, b->done);
   SHARPY_CUDA_TRY(cudaGetLastError());
+  // kernels of one round: reweight, covariance, systematic, save, gather, the
+  // local metric of every event (metric 2), NUTS, record
+  const int64_t round_kernels = 7 + (b->opt.metric == 2 ? E : 0);
+  b->launches = 1 + 2 * (int64_t)E;  // init, then prior draw and ln L of every event
   int rc = SHARPY_OK;
   for (int e = 0; e < E && !rc; ++e) {
     sharpy_ctx* c = b->ctx[e];
@@ -464,10 +482,12 @@ int sharpy_batch_run(sharpy_batch* b, const uint64_t* keys, sharpy_batch_result*
         };
         for (int i = 0; i < kNumSlotChoices; ++i) cands[i].slots = kSlotChoices[i];
         if ((rc = tune_slots(cands, kNumSlotChoices, trial, s, &b->slots))) return rc;
+        b->launches += 2 * kNumSlotChoices;  // one untimed and one timed trial per candidate
       }
     }
     if ((rc = enqueue_round_nuts(b, b->d_nuts, b->slots ? b->slots : guess, s))) return rc;
     if ((rc = enqueue_round_record(b, s))) return rc;
+    b->launches += round_kernels;
     ++nr;
   }
   if ((rc = capture_round(b, b->slots ? b->slots : guess))) return rc;
@@ -479,6 +499,7 @@ int sharpy_batch_run(sharpy_batch* b, const uint64_t* keys, sharpy_batch_result*
     if (!running || nr >= b->opt.max_stages) break;
     const int k = std::min(kRoundsPerCheck, b->opt.max_stages - nr);
     for (int i = 0; i < k; ++i) SHARPY_CUDA_TRY(cudaGraphLaunch(b->exec, s));
+    b->launches += k * b->graph_kernels;
     nr += k;
   }
   // results

@@ -50,8 +50,10 @@ def test_batch_matches_separate_runs(precision):
     assert rounds >= max(r["n_stages"] for r in res)
     _check_against_runs(b, ws, ctxs, keys, res, **kw)
     # a second run replays the cached graph without tuning and repeats itself
-    res2, _ = b.run(keys)
+    res2, rounds2 = b.run(keys)
     assert [r["lnz"] for r in res2] == [r["lnz"] for r in res]
+    # init, prior draw and ln L per event, then 7 kernels per round (eager or replayed)
+    assert b.launches == 1 + 2 * len(ws) + 7 * rounds2
 
 
 @pytest.mark.parametrize("metric", [1, 2])

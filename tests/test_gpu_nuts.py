@@ -184,3 +184,58 @@ def test_nuts_local_metric_taylorf2_matches_oracle():
                                    precision="fp64")
         _compare(t.cpu().numpy(), l.cpu().numpy(), api.Context.stats_to_numpy(st), ref[0], ref[1], ref[2],
                  ref[3], wid, frac=0.9, lf_frac=0.9)
+
+
+def _laplace_ensemble(w, model, ev, th_inj, beta, n, seed):
+    """Synthetic SMC-like state on the 11-D event: the dense inverse mass matrix is the inverse of the
+    oracle's local metric at the injection (Sec. 5); half the particles are drawn from N(theta_inj,
+    0.01 M^-1) (folded into the box by clipping), half from the prior."""
+    minv = np.linalg.inv(oracle.local_metric(model, ev, th_inj[None, :], beta)[0])
+    minv = 0.5 * (minv + minv.T)
+    lam, vec = np.linalg.eigh(minv)
+    z = np.random.default_rng(seed).standard_normal((n // 2, w.n_dim))
+    core = np.clip(th_inj + 0.1 * (z * np.sqrt(np.maximum(lam, 0.0))) @ vec.T, w.lo, w.hi)
+    return np.vstack([core, inputs.prior_draws(w, n - n // 2, seed)]), minv
+
+
+def test_nuts_bbh11_full_launch_sampled_parity():
+    """The 11-D three-detector event at full size: one launch over 2048 particles (8 slots per CTA, 256
+    CTAs: the geometry of the SMC run), depth 6, 2 transitions, a dense metric. Each particle's transition
+    is named by its index in the ensemble, so the oracle runs 64 sampled particles on their own. The step
+    gives trees that stop at a U-turn, at the depth limit and by divergence.
+
+    FP64 path: the trajectories agree with the oracle's as in the small cases. Mixed path: its gradient
+    differs from the FP64 one by ~1e-5 relative, and the 11-D dynamics amplify that over 63 leapfrogs, so
+    its trajectories are not the oracle's row by row. It is checked for what holds at any size: every
+    sampled returned state carries the oracle's ln L and gradient at its theta within the mixed-path
+    tolerances, and the ensemble's tree statistics match the FP64 launch's."""
+    G.require_gpu()
+    w = inputs.bbh11()
+    ev, ctx, th_inj, _ = G.event_pair(w)
+    model = helpers.oracle_model(w)
+    n, beta, eps = 2048, 0.5, 0.1
+    th, minv = _laplace_ensemble(w, model, ev, th_inj, beta, n, 31)
+    ids = np.sort(np.random.default_rng(5).choice(n, 64, replace=False))
+    out = {}
+    for prec in ("fp64", "mixed"):
+        t = G.to_dev(th)
+        l, g = ctx.loglike_grad(t, "fp64" if prec == "fp64" else prec)
+        if prec == "fp64":
+            l0, g0 = l.cpu().numpy(), g.cpu().numpy()
+        st = api.Context.stats_to_numpy(ctx.nuts_mutate(beta, t, l, g, G.to_dev(minv), eps, 6, 2, key=43,
+                                                        ctr=512, precision=prec))
+        out[prec] = (t.cpu().numpy(), l.cpu().numpy(), g.cpu().numpy(), st)
+        assert np.all(np.isfinite(out[prec][0])) and ctx.status() == 0
+    ref = oracle.nuts_mutate(model, ev, beta, th[ids], l0[ids], g0[ids], minv, eps, 6, 2, key=43, ctr=512,
+                             ids=ids)
+    lf = ref[3]["n_leapfrog"]
+    assert lf.min() < 20 and lf.max() == 126 and ref[3]["n_divergent"].sum() > 0  # all three tree endings
+    th64, l64, _, st64 = out["fp64"]
+    _compare(th64[ids], l64[ids], st64[ids], ref[0], ref[1], ref[2], ref[3], G.width(w), frac=0.9)
+    thm, lm, gm, stm = out["mixed"]
+    l2, g2 = oracle.loglike(model, ev, thm[ids])
+    assert np.max(np.abs(lm[ids] - l2)) <= 1e-3, np.max(np.abs(lm[ids] - l2))
+    assert np.max(G.grad_rel_err(gm[ids], g2, G.width(w))) <= 1e-4
+    for f, tol in (("n_leapfrog", 0.1), ("accept_sum", 0.1), ("n_divergent", 0.25)):
+        a, b = stm[f].astype(float).mean(), st64[f].astype(float).mean()
+        assert abs(a - b) <= tol * b + 1e-3, (f, a, b)

@@ -88,6 +88,25 @@ def test_nuts_stationarity(dense):
     assert np.allclose(l2, l3, rtol=1e-12, atol=1e-12) and np.allclose(g2, g3, rtol=1e-12, atol=1e-12)
 
 
+def test_nuts_subset_by_ensemble_index():
+    """A particle's transition depends on its position and its index in the ensemble only (the index names
+    its random numbers): rows run alone with their indices give the ensemble run's rows exactly, and the
+    same rows under other indices give other transitions."""
+    d = 2
+    model = helpers.gaussmix_model([-10.0] * d, [10.0] * d, [0.0], [[0.0] * d], [[1.0, 0.3]])
+    th = np.random.default_rng(12).standard_normal((300, d)) * np.array([1.0, 0.3])
+    lnl, g = oracle.loglike(model, None, th)
+    full = oracle.nuts_mutate(model, None, 1.0, th, lnl, g, None, 0.25, 6, 2, key=4, ctr=7)
+    ids = np.array([299, 0, 17, 150, 151])
+    sub = oracle.nuts_mutate(model, None, 1.0, th[ids], lnl[ids], g[ids], None, 0.25, 6, 2, key=4, ctr=7, ids=ids)
+    for a, b in zip(sub[:3], full[:3]):
+        assert np.array_equal(a, b[ids])
+    assert np.array_equal(sub[3]["n_leapfrog"], full[3]["n_leapfrog"][ids])
+    other = oracle.nuts_mutate(model, None, 1.0, th[ids], lnl[ids], g[ids], None, 0.25, 6, 2, key=4, ctr=7,
+                               ids=ids + 1)
+    assert not np.array_equal(other[0], full[0][ids])
+
+
 def test_nuts_per_particle_metric_stationarity():
     """Each particle with its own (random, fixed) dense metric: one transition from the target still
     yields the target (KS per coordinate)."""
