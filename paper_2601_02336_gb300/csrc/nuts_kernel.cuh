@@ -2,19 +2,25 @@
 // variant with biased progressive sampling at the top level and the
 // generalised U-turn criterion on every completed sub-tree).
 //
-// One CTA of kNutsWarps warps owns SLOTS (8 or 16) particles for the whole
-// call; SLOTS is chosen from N so that about two CTAs share each SM (their
-// serial per-particle phases then overlap with each other's sweeps) while warp
-// 0's per-particle phase runs on as many lanes as possible (an FP64 warp
-// instruction costs the same pipe time whatever its active-lane count).
-// Lane s of warp 0 runs the NUTS state machine of slot s: the trajectory is
-// grown one leapfrog at a time (iteratively, no recursion), and every leapfrog
-// needs one likelihood+gradient evaluation. Each "tick" of the CTA: warp 0
-// computes the prologue of every pending evaluation (lane-parallel), each warp
-// sweeps the bins of one pending particle, warp 0 runs the epilogues and
-// advances the state machines to their next evaluation. Particles with shallow
-// trees finish early and leave their lane idle; the tree state of every slot
-// lives in shared memory ([field][dim][slot], conflict-free across lanes).
+// One CTA of kNutsWarps warps owns SLOTS (8, 16 or 32) particles for the
+// whole call; the slot count is autotuned (about two CTAs share each SM, so
+// their serial per-particle phases overlap with each other's sweeps). Every
+// slot's trajectory is grown one leapfrog at a time (iteratively, no
+// recursion), and every leapfrog needs one likelihood+gradient evaluation.
+// Each "tick" of the CTA has three phases between barriers:
+//   A  the prologue of every pending evaluation, lane = slot: the phase half
+//      (PN coefficients, k_ISCO; FP64) on the control warp, the sky half
+//      (responses, delays, amplitude) on its neighbour, a warp on another SM
+//      sub-partition;
+//   B  each warp sweeps the bins of the next pending particle, longest first;
+//   C  lane l < SLOTS/kNutsWarps of warp w owns slot w SLOTS/kNutsWarps + l:
+//      the epilogue, the tree update and the first half of the next leapfrog.
+// An FP64 warp instruction costs the same pipe time whatever its active-lane
+// count, and a warp runs the union of its lanes' branches of the state
+// machine: spreading both over the sub-partitions shortens the serial part of
+// a tick. Particles with shallow trees finish early and leave their slot idle;
+// the tree state of every slot lives in shared memory ([field][dim][slot],
+// conflict-free across lanes).
 //
 // Precision of the tree state (template VT): positions theta and the potential
 // energy are FP64 on every path. The FP64 path keeps momenta, velocities,
@@ -90,8 +96,8 @@ enum { METRIC_IDENTITY = 0, METRIC_DIAGONAL = 1, METRIC_DENSE = 2 };
 
 template <int SLOTS, class VT>
 struct NutsShared {
-  double pos[P_COUNT][kMaxDim][SLOTS];
-  VT vec[F_COUNT][kMaxDim][SLOTS];
+  double pos[P_COUNT][SLOTS][kMaxDim];  // [field][slot][dim]: a slot's lanes read consecutive words
+  VT vec[F_COUNT][SLOTS][kMaxDim];
   // metric: minv and its Cholesky factor, [kMaxDim][kMaxDim][mstride] each, after
   // NutsSmem in dynamic shared memory: one copy (shared metric, mstride = 1) or
   // one per slot (per-particle metric, mstride = SLOTS)
@@ -148,7 +154,8 @@ __device__ __forceinline__ void draw2(uint64_t key, uint32_t c0, uint32_t c1, ui
   *u1 = ((float)(x[2] >> 8) + 0.5f) * 5.9604644775390625e-8f;
 }
 
-// Per-slot state machine (registers of lane s of warp 0).
+// Per-slot state machine: the scalars live in registers, identical in every
+// lane of the slot's lane group.
 template <class VT>
 struct Slot {
   int64_t pid;
@@ -167,101 +174,175 @@ struct Slot {
   int st_depth, st_leap, st_div;
 };
 
+// Lanes per slot and dimensions per lane of the state machine: a slot's G
+// lanes each own the dimensions t, t + G, ... (t < G) of its vectors, padded
+// to kLaneDims. Sums over the dimensions follow one fixed tree over kLaneDims
+// terms (pairs d, d + 8 first, then + 4, + 2, + 1) whatever G is, so a
+// trajectory does not depend on the slot count.
+constexpr int kLaneDims = 16;
+static_assert(kMaxDim <= kLaneDims, "one fixed reduction tree over at most 16 dimensions");
+
 template <int PREC, int NDET, int SLOTS>
 struct Nuts {
   using VT = typename std::conditional<PREC == SHARPY_FP64, double, float>::type;
+  static constexpr int SPW = SLOTS / kNutsWarps;  // slots per warp
+  static constexpr int G = 32 / SPW;              // lanes per slot: 16, 8, 4
+  static constexpr int DPL = kLaneDims / G;       // dimensions per lane: 1, 2, 4
   const NutsArgs& A;
   NutsShared<SLOTS, VT>& S;
-  int s;  // slot
+  int s;        // slot
+  int t;        // lane within the slot's group
+  unsigned gm;  // the group's lanes
   int D;
-  __device__ Nuts(const NutsArgs& a, NutsShared<SLOTS, VT>& sh, int slot) : A(a), S(sh), s(slot), D(a.m.n_dim) {}
-  __device__ VT& V(int f, int d) { return S.vec[f][d][s]; }
+  __device__ Nuts(const NutsArgs& a, NutsShared<SLOTS, VT>& sh, int slot, int lane_in_group, unsigned mask)
+      : A(a), S(sh), s(slot), t(lane_in_group), gm(mask), D(a.m.n_dim) {}
+  __device__ int dim(int k) const { return t + G * k; }
+  __device__ bool has(int k) const { return t + G * k < D; }
+  __device__ VT& V(int f, int d) { return S.vec[f][s][d]; }
   __device__ VT& MI(int i, int j) { return S.mmin[(i * kMaxDim + j) * S.mstride + (S.mstride > 1 ? s : 0)]; }
   __device__ VT& CH(int i, int j) { return S.mchol[(i * kMaxDim + j) * S.mstride + (S.mstride > 1 ? s : 0)]; }
-  __device__ double& X(int f, int d) { return S.pos[f][d][s]; }
+  __device__ double& X(int f, int d) { return S.pos[f][s][d]; }
+  __device__ void sync() { __syncwarp(gm); }
 
-  // v = Minv r for the momentum stored in field f
+  // Sum over the slot's dimensions of this lane's partial terms p[0..DPL).
+  template <class T>
+  __device__ T gsum(const T* p) {
+    T x;
+    if constexpr (DPL == 1)
+      x = p[0];
+    else if constexpr (DPL == 2)
+      x = p[0] + p[1];
+    else
+      x = (p[0] + p[2]) + (p[1] + p[3]);
+#pragma unroll
+    for (int m = G / 2; m >= 1; m >>= 1) x += __shfl_xor_sync(gm, x, m);
+    return x;
+  }
+
+  // v = Minv r for the momentum stored in field f (this lane's dimensions)
   __device__ void velocity(int f, VT* v) {
-    if (S.metric_kind == METRIC_IDENTITY) {
-      for (int i = 0; i < D; ++i) v[i] = V(f, i);
-    } else if (S.metric_kind == METRIC_DIAGONAL) {
-      for (int i = 0; i < D; ++i) v[i] = MI(i, i) * V(f, i);
-    } else {
-      for (int i = 0; i < D; ++i) {
+    const int kind = S.metric_kind;
+    if (kind == METRIC_DENSE) sync();  // every lane reads the whole momentum
+#pragma unroll
+    for (int k = 0; k < DPL; ++k) {
+      const int d = dim(k);
+      v[k] = VT(0);
+      if (!has(k)) continue;
+      if (kind == METRIC_IDENTITY) {
+        v[k] = V(f, d);
+      } else if (kind == METRIC_DIAGONAL) {
+        v[k] = MI(d, d) * V(f, d);
+      } else {
         VT acc = VT(0);
-        for (int j = 0; j < D; ++j) acc += MI(i, j) * V(f, j);
-        v[i] = acc;
+        for (int j = 0; j < D; ++j) acc += MI(d, j) * V(f, j);
+        v[k] = acc;
       }
     }
   }
   __device__ VT dot(const VT* a, int f) {
-    VT k = VT(0);
-    for (int i = 0; i < D; ++i) k += a[i] * V(f, i);
-    return k;
+    VT p[DPL];
+#pragma unroll
+    for (int k = 0; k < DPL; ++k) p[k] = has(k) ? a[k] * V(f, dim(k)) : VT(0);
+    return gsum(p);
   }
   __device__ VT dotv(const VT* a, const VT* b) {
-    VT k = VT(0);
-    for (int i = 0; i < D; ++i) k += a[i] * b[i];
-    return k;
+    VT p[DPL];
+#pragma unroll
+    for (int k = 0; k < DPL; ++k) p[k] = has(k) ? a[k] * b[k] : VT(0);
+    return gsum(p);
   }
   // ln pi (FP64 total) and grad ln pi with the constant terms precomputed.
   // CHECK = false: x is known to lie in the box (it came out of boundary()).
   template <bool CHECK = true>
   __device__ double prior(const double* x, VT* g) {
     const DevModel& m = A.m;
-    double lp = S.lp_const;
+    double p[DPL];
     bool inside = true;
-    for (int i = 0; i < D; ++i) {
-      g[i] = VT(0);
-      if (CHECK && !(x[i] >= m.lo[i] && x[i] <= m.hi[i])) inside = false;
-      if (m.prior[i] == SHARPY_PRIOR_POWER2) {
-        const VT xi = (VT)x[i];
-        lp += (double)(VT(2) * vlog(xi));
-        g[i] = VT(2) / xi;
+#pragma unroll
+    for (int k = 0; k < DPL; ++k) {
+      const int d = dim(k);
+      g[k] = VT(0);
+      p[k] = 0.0;
+      if (!has(k)) continue;
+      if (CHECK && !(x[k] >= m.lo[d] && x[k] <= m.hi[d])) inside = false;
+      if (m.prior[d] == SHARPY_PRIOR_POWER2) {
+        const VT xi = (VT)x[k];
+        p[k] = (double)(VT(2) * vlog(xi));
+        g[k] = VT(2) / xi;
       }
     }
+    const double lp = S.lp_const + gsum(p);
+    if (CHECK) inside = __all_sync(gm, inside);
     return inside ? lp : -INFINITY;
   }
 
   // Boundary maps on the pending leaf (P_N, F_NR). False if not finite.
+  // Periodic dimensions wrap lane-parallel (no momentum change); reflections,
+  // whose momentum update reads the whole velocity, run dimension by
+  // dimension in order (rare: a leaf outside the box).
   __device__ bool boundary() {
     const DevModel& m = A.m;
-    for (int i = 0; i < D; ++i) {
-      double x = X(P_N, i);
+    bool ok = true, reflect = false;
+#pragma unroll
+    for (int k = 0; k < DPL; ++k) {
+      const int d = dim(k);
+      if (!has(k)) continue;
+      double x = X(P_N, d);
       const long long b = __double_as_longlong(x);
-      if ((b & 0x7ff0000000000000LL) == 0x7ff0000000000000LL) return false;  // not finite
-      const bool periodic = m.boundary[i] == SHARPY_BOUND_PERIODIC;
-      if (!periodic) {
-        const long long k = okey(x);
-        if (k >= S.lokey[i] && k <= S.hikey[i]) continue;  // inside: nothing to do
+      if ((b & 0x7ff0000000000000LL) == 0x7ff0000000000000LL) {  // not finite
+        ok = false;
+        continue;
       }
-      double lo = m.lo[i], hi = m.hi[i];
-      if (periodic) {
-        // lo + ((x - lo) mod w): for |x - lo| < 2w one exact subtraction or
-        // addition gives fmod's result; fmod only for larger excursions
-        const double w = hi - lo;
-        double t = x - lo;
-        if (t >= w)
-          t = t < 2.0 * w ? t - w : fmod(t, w);
-        else if (t < 0.0)
-          t = t >= -w ? t : fmod(t, w);
-        if (t < 0.0) t += w;
-        X(P_N, i) = lo + t;
-      } else {
-        int flips = 0;
+      if (m.boundary[d] != SHARPY_BOUND_PERIODIC) {
+        const long long q = okey(x);
+        if (q < S.lokey[d] || q > S.hikey[d]) reflect = true;
+        continue;
+      }
+      // lo + ((x - lo) mod w): for |x - lo| < 2w one exact subtraction or
+      // addition gives fmod's result; fmod only for larger excursions
+      const double lo = m.lo[d], w = m.hi[d] - lo;
+      double r = x - lo;
+      if (r >= w)
+        r = r < 2.0 * w ? r - w : fmod(r, w);
+      else if (r < 0.0)
+        r = r >= -w ? r : fmod(r, w);
+      if (r < 0.0) r += w;
+      X(P_N, d) = lo + r;
+    }
+    if (!__all_sync(gm, ok)) return false;
+    if (!__any_sync(gm, reflect)) return true;
+    for (int i = 0; i < D; ++i) {
+      if (m.boundary[i] == SHARPY_BOUND_PERIODIC) continue;
+      const double lo = m.lo[i], hi = m.hi[i];
+      int flips = 0;
+      if (t == i % G) {
+        double x = X(P_N, i);
         while ((x < lo || x > hi) && flips < 100) {
           x = x < lo ? 2.0 * lo - x : 2.0 * hi - x;
           ++flips;
         }
-        if (x < lo || x > hi) return false;
-        X(P_N, i) = x;
-        if (flips & 1) {
-          VT v[kMaxDim];
-          velocity(F_NR, v);
-          V(F_NR, i) = V(F_NR, i) - VT(2) * v[i] / MI(i, i);
+        if (x < lo || x > hi) flips = -1;
+        else X(P_N, i) = x;
+      }
+      flips = __shfl_sync(gm, flips, i % G, G);
+      if (flips < 0) return false;
+      if (flips & 1) {
+        sync();
+        VT vi;
+        if (S.metric_kind == METRIC_IDENTITY) {
+          vi = V(F_NR, i);
+        } else if (S.metric_kind == METRIC_DIAGONAL) {
+          vi = MI(i, i) * V(F_NR, i);
+        } else {
+          VT acc = VT(0);
+          for (int j = 0; j < D; ++j) acc += MI(i, j) * V(F_NR, j);
+          vi = acc;
         }
+        sync();
+        if (t == i % G) V(F_NR, i) = V(F_NR, i) - VT(2) * vi / MI(i, i);
       }
     }
+    sync();
     return true;
   }
 
@@ -270,10 +351,14 @@ struct Nuts {
     const int pth = dir > 0 ? P_R : P_L, fr = dir > 0 ? F_RR : F_LR, fgu = dir > 0 ? F_RGU : F_LGU;
     const double h = dir * S.eps;
     const VT hv = (VT)h;
-    for (int i = 0; i < D; ++i) V(F_NR, i) = V(fr, i) - VT(0.5) * hv * V(fgu, i);
-    VT v[kMaxDim];
+#pragma unroll
+    for (int k = 0; k < DPL; ++k)
+      if (has(k)) V(F_NR, dim(k)) = V(fr, dim(k)) - VT(0.5) * hv * V(fgu, dim(k));
+    VT v[DPL];
     velocity(F_NR, v);
-    for (int i = 0; i < D; ++i) X(P_N, i) = X(pth, i) + h * (double)v[i];
+#pragma unroll
+    for (int k = 0; k < DPL; ++k)
+      if (has(k)) X(P_N, dim(k)) = X(pth, dim(k)) + h * (double)v[k];
     return boundary();
   }
 
@@ -283,45 +368,62 @@ struct Nuts {
     sl.dir = u0 < VT(0.5) ? -1 : 1;
     sl.n = 0;
     sl.logw_sub = -INFINITY;
-    for (int i = 0; i < D; ++i) V(F_RHOS, i) = VT(0);
+#pragma unroll
+    for (int k = 0; k < DPL; ++k)
+      if (has(k)) V(F_RHOS, dim(k)) = VT(0);
   }
 
   // Start transition sl.t from the current point (P_P, F_PGL, lnl_p).
   __device__ void start_transition(Slot<VT>& sl) {
     const uint32_t step = A.ctr + (uint32_t)sl.t;
-    VT z[kMaxDim + 1];
-    for (int p = 0; 2 * p < D; ++p) {
+    // z ~ N(0, I): dimensions 2p and 2p + 1 from the normal pair p
+#pragma unroll
+    for (int k = 0; k < DPL; ++k) {
+      const int d = dim(k);
+      if (!has(k)) continue;
       VT u0, u1;
-      draw2(A.key, (uint32_t)sl.pid, step, RNG_MOMENTUM, (uint32_t)p, &u0, &u1);
-      VT r = vsqrt(VT(-2) * vlog(u0));
+      draw2(A.key, (uint32_t)sl.pid, step, RNG_MOMENTUM, (uint32_t)(d >> 1), &u0, &u1);
+      const VT r = vsqrt(VT(-2) * vlog(u0));
       VT sn, cs;
       vsincospi(VT(2) * u1, &sn, &cs);
-      z[2 * p] = r * cs;
-      z[2 * p + 1] = r * sn;
+      V(F_LR, d) = (d & 1) ? r * sn : r * cs;
     }
-    // r ~ N(0, M), M = Minv^{-1} = (L L^T)^{-1}: solve L^T r = z
-    for (int i = D - 1; i >= 0; --i) {
-      VT acc = z[i];
-      for (int j = i + 1; j < D; ++j) acc -= CH(j, i) * V(F_LR, j);
-      V(F_LR, i) = acc / CH(i, i);
+    // r ~ N(0, M), M = Minv^{-1} = (L L^T)^{-1}: solve L^T r = z (identity: r = z)
+    if (S.metric_kind == METRIC_DIAGONAL) {
+#pragma unroll
+      for (int k = 0; k < DPL; ++k)
+        if (has(k)) V(F_LR, dim(k)) = V(F_LR, dim(k)) / CH(dim(k), dim(k));
+    } else if (S.metric_kind == METRIC_DENSE) {
+      sync();
+      if (t == 0)
+        for (int i = D - 1; i >= 0; --i) {
+          VT acc = V(F_LR, i);
+          for (int j = i + 1; j < D; ++j) acc -= CH(j, i) * V(F_LR, j);
+          V(F_LR, i) = acc / CH(i, i);
+        }
+      sync();
     }
     // U and grad U at the current point
-    double x[kMaxDim];
-    VT glp[kMaxDim], v0[kMaxDim];
-    for (int i = 0; i < D; ++i) x[i] = X(P_P, i);
+    double x[DPL];
+    VT glp[DPL], v0[DPL];
+#pragma unroll
+    for (int k = 0; k < DPL; ++k) x[k] = has(k) ? X(P_P, dim(k)) : 0.0;
     const double lp = prior(x, glp);
     const double u_cur = -S.beta * sl.lnl_p - lp;
     const VT bv = (VT)S.beta;
     velocity(F_LR, v0);
-    for (int i = 0; i < D; ++i) {
-      X(P_L, i) = x[i];
-      X(P_R, i) = x[i];
-      V(F_LGU, i) = -bv * V(F_PGL, i) - glp[i];
-      V(F_LV, i) = v0[i];
-      V(F_RR, i) = V(F_LR, i);
-      V(F_RGU, i) = V(F_LGU, i);
-      V(F_RV, i) = v0[i];
-      V(F_RHO, i) = V(F_LR, i);
+#pragma unroll
+    for (int k = 0; k < DPL; ++k) {
+      const int d = dim(k);
+      if (!has(k)) continue;
+      X(P_L, d) = x[k];
+      X(P_R, d) = x[k];
+      V(F_LGU, d) = -bv * V(F_PGL, d) - glp[k];
+      V(F_LV, d) = v0[k];
+      V(F_RR, d) = V(F_LR, d);
+      V(F_RGU, d) = V(F_LGU, d);
+      V(F_RV, d) = v0[k];
+      V(F_RHO, d) = V(F_LR, d);
     }
     sl.h0 = u_cur + (double)(VT(0.5) * dot(v0, F_LR));
     sl.logw = VT(0);
@@ -342,19 +444,23 @@ struct Nuts {
 
   // Advance until the next evaluation is pending (true) or the slot is done.
   // have_leaf: a leaf evaluation just finished (P_N, F_NR hold its position and
-  // half-step momentum; lnl_new, gl_new, lp_new, glp_new its values).
+  // half-step momentum; lnl_new, gl_new, lp_new, glp_new its values, gl_new
+  // and glp_new for this lane's dimensions).
   __device__ bool advance(Slot<VT>& sl, bool have_leaf, const VT* gl_new, double lp_new, const VT* glp_new) {
     if (have_leaf) {
       // complete the leapfrog
       const VT h = (VT)(sl.dir * S.eps);
       const VT bv = (VT)S.beta;
-      VT gu[kMaxDim];
-      for (int i = 0; i < D; ++i) {
-        gu[i] = -bv * gl_new[i] - glp_new[i];
-        V(F_NR, i) = V(F_NR, i) - VT(0.5) * h * gu[i];
+      VT gu[DPL];
+#pragma unroll
+      for (int k = 0; k < DPL; ++k) {
+        gu[k] = VT(0);
+        if (!has(k)) continue;
+        gu[k] = -bv * gl_new[k] - glp_new[k];
+        V(F_NR, dim(k)) = V(F_NR, dim(k)) - VT(0.5) * h * gu[k];
       }
       const double u_new = -S.beta * sl.lnl_new - lp_new;
-      VT vn[kMaxDim];
+      VT vn[DPL];
       velocity(F_NR, vn);
       const double dH = u_new + (double)(VT(0.5) * dot(vn, F_NR)) - sl.h0;
       sl.n_leaf += 1;
@@ -368,36 +474,46 @@ struct Nuts {
         // the leaf becomes the end of the tree in direction dir
         const int pth = sl.dir > 0 ? P_R : P_L, fr = sl.dir > 0 ? F_RR : F_LR, fgu = sl.dir > 0 ? F_RGU : F_LGU;
         const int fv = sl.dir > 0 ? F_RV : F_LV;
-        for (int i = 0; i < D; ++i) {
-          X(pth, i) = X(P_N, i);
-          V(fr, i) = V(F_NR, i);
-          V(fgu, i) = gu[i];
-          V(fv, i) = vn[i];
+#pragma unroll
+        for (int k = 0; k < DPL; ++k) {
+          const int d = dim(k);
+          if (!has(k)) continue;
+          X(pth, d) = X(P_N, d);
+          V(fr, d) = V(F_NR, d);
+          V(fgu, d) = gu[k];
+          V(fv, d) = vn[k];
         }
         const VT lw = (VT)(-dH);
         const VT lw_new = logaddexp(sl.logw_sub, lw);
         VT u0, u1;
         draw2(A.key, (uint32_t)sl.pid, A.ctr + (uint32_t)sl.t, RNG_LEAF, sl.leaf_ctr++, &u0, &u1);
         if (u0 < vexp(lw - lw_new)) {
-          for (int i = 0; i < D; ++i) {
-            X(P_S, i) = X(P_N, i);
-            V(F_SGL, i) = gl_new[i];
+#pragma unroll
+          for (int k = 0; k < DPL; ++k) {
+            if (!has(k)) continue;
+            X(P_S, dim(k)) = X(P_N, dim(k));
+            V(F_SGL, dim(k)) = gl_new[k];
           }
           sl.lnl_s = sl.lnl_new;
         }
         sl.logw_sub = lw_new;
         for (int lvl = 1; lvl <= sl.depth; ++lvl)
           if ((sl.n & ((1L << lvl) - 1)) == 0)
-            for (int i = 0; i < D; ++i) {
-              V(F_RS0 + lvl - 1, i) = V(F_RHOS, i);
-              V(F_RF0 + lvl - 1, i) = vn[i];
+#pragma unroll
+            for (int k = 0; k < DPL; ++k) {
+              if (!has(k)) continue;
+              V(F_RS0 + lvl - 1, dim(k)) = V(F_RHOS, dim(k));
+              V(F_RF0 + lvl - 1, dim(k)) = vn[k];
             }
-        for (int i = 0; i < D; ++i) V(F_RHOS, i) += V(F_NR, i);
+#pragma unroll
+        for (int k = 0; k < DPL; ++k)
+          if (has(k)) V(F_RHOS, dim(k)) += V(F_NR, dim(k));
         bool ok = true;
         for (int lvl = 1; lvl <= sl.depth && ok; ++lvl)
           if (((sl.n + 1) & ((1L << lvl) - 1)) == 0) {
-            VT rb[kMaxDim];
-            for (int i = 0; i < D; ++i) rb[i] = V(F_RHOS, i) - V(F_RS0 + lvl - 1, i);
+            VT rb[DPL];
+#pragma unroll
+            for (int k = 0; k < DPL; ++k) rb[k] = has(k) ? V(F_RHOS, dim(k)) - V(F_RS0 + lvl - 1, dim(k)) : VT(0);
             if (!(dot(rb, F_RF0 + lvl - 1) > VT(0) && dotv(rb, vn) > VT(0))) ok = false;
           }
         if (!ok) {
@@ -415,17 +531,22 @@ struct Nuts {
         // sub-tree complete: biased progressive sampling at the top level
         draw2(A.key, (uint32_t)sl.pid, A.ctr + (uint32_t)sl.t, RNG_TOP, (uint32_t)sl.depth, &u0, &u1);
         if (u0 < vexp(sl.logw_sub - sl.logw)) {
-          for (int i = 0; i < D; ++i) {
-            X(P_P, i) = X(P_S, i);
-            V(F_PGL, i) = V(F_SGL, i);
+#pragma unroll
+          for (int k = 0; k < DPL; ++k) {
+            if (!has(k)) continue;
+            X(P_P, dim(k)) = X(P_S, dim(k));
+            V(F_PGL, dim(k)) = V(F_SGL, dim(k));
           }
           sl.lnl_p = sl.lnl_s;
         }
         sl.logw = logaddexp(sl.logw, sl.logw_sub);
-        VT rho[kMaxDim];
-        for (int i = 0; i < D; ++i) {
-          V(F_RHO, i) += V(F_RHOS, i);
-          rho[i] = V(F_RHO, i);
+        VT rho[DPL];
+#pragma unroll
+        for (int k = 0; k < DPL; ++k) {
+          rho[k] = VT(0);
+          if (!has(k)) continue;
+          V(F_RHO, dim(k)) += V(F_RHOS, dim(k));
+          rho[k] = V(F_RHO, dim(k));
         }
         sl.depth += 1;
         if (!(dot(rho, F_LV) > VT(0) && dot(rho, F_RV) > VT(0)) || sl.depth >= A.max_depth) {
@@ -579,35 +700,49 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(const __grid_c
   }
   __syncthreads();
 
+  // Slot ownership: warp w runs the state machines of slots w SPW ..
+  // w SPW + SPW - 1, each on a group of G = 32 / SPW lanes that share its
+  // vectors' dimensions, so the per-slot phases of a tick (epilogue, tree
+  // update, next leapfrog) run on all four SM sub-partitions at once.
+  using NT = Nuts<PREC, NDET, SLOTS>;
+  constexpr int SPW = NT::SPW, G = NT::G, DPL = NT::DPL;
+  static_assert(SLOTS % kNutsWarps == 0, "slots are shared evenly by the warps");
+  const int my = warp * SPW + lane / G;  // this lane's slot
+  const int tg = lane % G;                // its lane within the slot's group
+  const unsigned gmask = (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << (lane - tg);
   Slot<VT> sl;
-  bool active = false;
-  if (warp == cw && lane < SLOTS) {
-    Nuts<PREC, NDET, SLOTS> nu(A, S, lane);
-    sl.pid = (int64_t)s_block * SLOTS + lane;
+  {
+    NT nu(A, S, my, tg, gmask);
+    sl.pid = (int64_t)s_block * SLOTS + my;
     sl.t = 0;
     sl.done = 1;
     sl.st_acc = sl.st_bins = 0.0;
     sl.st_depth = sl.st_leap = sl.st_div = 0;
+    bool active = false;
     if (sl.pid < A.n) {
-      for (int i = 0; i < D; ++i) {
-        nu.X(P_P, i) = A.theta[sl.pid * D + i];
-        nu.V(F_PGL, i) = (VT)A.grad[sl.pid * D + i];
+#pragma unroll
+      for (int k = 0; k < DPL; ++k) {
+        const int d = nu.dim(k);
+        if (!nu.has(k)) continue;
+        nu.X(P_P, d) = A.theta[sl.pid * D + d];
+        nu.V(F_PGL, d) = (VT)A.grad[sl.pid * D + d];
+        if (A.pminv) {
+          const double* pm = A.pminv + sl.pid * D * D;
+          const double* pc = A.pchol + sl.pid * D * D;
+          for (int j = 0; j < D; ++j) {
+            nu.MI(d, j) = (VT)pm[d * D + j];
+            nu.CH(d, j) = (VT)pc[d * D + j];
+          }
+        }
       }
       sl.lnl_p = A.lnl[sl.pid];
-      if (A.pminv) {
-        const double* pm = A.pminv + sl.pid * D * D;
-        const double* pc = A.pchol + sl.pid * D * D;
-        for (int i = 0; i < D; ++i)
-          for (int j = 0; j < D; ++j) {
-            nu.MI(i, j) = (VT)pm[i * D + j];
-            nu.CH(i, j) = (VT)pc[i * D + j];
-          }
-      }
+      nu.sync();
       sl.done = 0;
       active = nu.advance(sl, false, nullptr, 0.0, nullptr);
     }
-    S.pending[lane] = active ? 1 : 0;
+    if (tg == 0) S.pending[my] = active ? 1 : 0;
   }
+  __syncthreads();
   const long max_ticks = (long)A.n_steps * ((1L << A.max_depth) + 1) + 4;
   for (long tick = 0;; ++tick) {
     // warp 0: any pending evaluation left?
@@ -622,20 +757,15 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(const __grid_c
     }
     __syncthreads();
     if (!S.alive) break;
-    // (A) prologues (GW) or direct evaluations (Gaussian mixture)
-    VT gl_new[kMaxDim], glp_new[kMaxDim];
-    double lp_new = 0.0;
-    if (warp == cw && lane < SLOTS && S.pending[lane]) {
-      Nuts<PREC, NDET, SLOTS> nu(A, S, lane);
+    // (A) prologues (GW models; lane = slot): the phase half on the control
+    // warp, the sky half on its neighbour, on another sub-partition
+    if (gw && (warp == cw || warp == (cw ^ 1)) && lane < SLOTS && S.pending[lane]) {
       double x[kMaxDim];
-      for (int i = 0; i < D; ++i) x[i] = nu.X(P_N, i);
-      if (gw) {
-        prologue<DT, true, PREC == SHARPY_MIXED_SPLIT>(A.m, A.ev, x, sc[lane], ec[lane]);
-      } else {
-        double g[kMaxDim];
-        gaussmix(A.m, x, &sl.lnl_new, g);
-        for (int i = 0; i < D; ++i) gl_new[i] = (VT)g[i];
-      }
+      for (int i = 0; i < D; ++i) x[i] = S.pos[P_N][lane][i];
+      if (warp == cw)
+        prologue_phase<DT, true, PREC == SHARPY_MIXED_SPLIT>(A.m, A.ev, x, sc[lane], ec[lane]);
+      else
+        prologue_sky<DT, true, PREC == SHARPY_MIXED_SPLIT>(A.m, A.ev, x, sc[lane], ec[lane]);
     }
     if (gw && warp == cw) {
       // order this tick's sweeps by decreasing k_ISCO (ties: slot order)
@@ -668,35 +798,53 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(const __grid_c
       }
     }
     __syncthreads();
-    // (C) epilogues and state machines
-    if (warp == cw && lane < SLOTS && S.pending[lane]) {
-      Nuts<PREC, NDET, SLOTS> nu(A, S, lane);
-      double x[kMaxDim];
-      for (int i = 0; i < D; ++i) x[i] = nu.X(P_N, i);
+    // (C) epilogues (or direct evaluations: Gaussian mixture) and state
+    // machines, each on its slot's lane group (the scalar parts run
+    // identically on every lane of the group)
+    if (S.pending[my]) {
+      NT nu(A, S, my, tg, gmask);
+      VT gl_new[DPL], glp_new[DPL];
+      double x[DPL];
+#pragma unroll
+      for (int k = 0; k < DPL; ++k) x[k] = nu.has(k) ? nu.X(P_N, nu.dim(k)) : 0.0;
       if (gw) {
         DT gph[SHARPY_NPHYS];
         sl.lnl_new = NAN;
-        if (sc[lane].ok) {
-          epilogue<DT, true>(A.ev, sc[lane], ec[lane], mom[lane], &sl.lnl_new, gph);
-          sl.st_bins += (double)(sc[lane].kisco + 1) * A.ev.n_det;
+        if (sc[my].ok) {
+          epilogue<DT, true>(A.ev, sc[my], ec[my], mom[my], &sl.lnl_new, gph);
+          sl.st_bins += (double)(sc[my].kisco + 1) * A.ev.n_det;
         }
-        for (int i = 0; i < D; ++i) gl_new[i] = sc[lane].ok ? gph[A.m.phys[i]] : (VT)NAN;
+#pragma unroll
+        for (int k = 0; k < DPL; ++k)
+          gl_new[k] = !nu.has(k) ? VT(0) : sc[my].ok ? (VT)gph[A.m.phys[nu.dim(k)]] : (VT)NAN;
+      } else {
+        double xa[kMaxDim], g[kMaxDim];
+        for (int i = 0; i < D; ++i) xa[i] = nu.X(P_N, i);
+        gaussmix(A.m, xa, &sl.lnl_new, g);
+#pragma unroll
+        for (int k = 0; k < DPL; ++k) gl_new[k] = nu.has(k) ? (VT)g[nu.dim(k)] : VT(0);
       }
-      lp_new = nu.template prior<false>(x, glp_new);
+      const double lp_new = nu.template prior<false>(x, glp_new);
       if (!isfinite(sl.lnl_new)) sl.lnl_new = -INFINITY;  // rejected leaf (U = +inf)
-      for (int i = 0; i < D; ++i)
-        if (!isfinite(gl_new[i])) gl_new[i] = VT(0);
-      bool more = nu.advance(sl, true, gl_new, lp_new, glp_new);
-      S.pending[lane] = more ? 1 : 0;
+#pragma unroll
+      for (int k = 0; k < DPL; ++k)
+        if (!isfinite(gl_new[k])) gl_new[k] = VT(0);
+      const bool more = nu.advance(sl, true, gl_new, lp_new, glp_new);
+      if (tg == 0) S.pending[my] = more ? 1 : 0;
     }
+    __syncthreads();  // the control warp reads every slot's pending flag next
   }
   // write back
-  if (warp == cw && lane < SLOTS && sl.pid < A.n) {
-    Nuts<PREC, NDET, SLOTS> nu(A, S, lane);
-    for (int i = 0; i < D; ++i) {
-      A.theta[sl.pid * D + i] = nu.X(P_P, i);
-      A.grad[sl.pid * D + i] = (double)nu.V(F_PGL, i);
+  if (sl.pid < A.n) {
+    NT nu(A, S, my, tg, gmask);
+#pragma unroll
+    for (int k = 0; k < DPL; ++k) {
+      if (!nu.has(k)) continue;
+      A.theta[sl.pid * D + nu.dim(k)] = nu.X(P_P, nu.dim(k));
+      A.grad[sl.pid * D + nu.dim(k)] = (double)nu.V(F_PGL, nu.dim(k));
     }
+  }
+  if (tg == 0 && sl.pid < A.n) {
     A.lnl[sl.pid] = sl.lnl_p;
     if (A.stats) {
       sharpy_nuts_stats st;

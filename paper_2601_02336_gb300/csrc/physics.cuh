@@ -357,16 +357,23 @@ __device__ __forceinline__ int isco_bin(const DevEvent& ev, double fisco) {
   return (int)k;
 }
 
-// theta (free dims) -> sweep and epilogue coefficients.
+// Whether theta lies in the model's domain (both halves of the prologue test it).
+__device__ __forceinline__ bool phys_ok(const double* ph) {
+  return ph[SHARPY_MC] > 0.0 && ph[SHARPY_Q] > 0.0 && ph[SHARPY_DL] > 0.0 && fabs(ph[SHARPY_SINDEC]) <= 1.0 &&
+         fabs(ph[SHARPY_COSI]) <= 1.0;
+}
+
+// The prologue in two independent halves, so that two warps can run them at
+// once (the persistent NUTS kernel does): the phase half writes alpha, c0,
+// k_ISCO, ok (and their Jacobians); the sky half writes the amplitude, the
+// responses C_a, the delays tau_a (and theirs). Neither reads what the other
+// writes.
 template <class DT, bool GRAD, bool SPLIT = false>
-__device__ void prologue(const DevModel& m, const DevEvent& ev, const double* th, SweepCoef& sc,
-                         EpiCoef<DT>& ec) {
+__device__ void prologue_phase(const DevModel& m, const DevEvent& ev, const double* th, SweepCoef& sc,
+                               EpiCoef<DT>& ec) {
   double ph[SHARPY_NPHYS];
   to_physical(m, th, ph);
-  sc.ok = (ph[SHARPY_MC] > 0.0 && ph[SHARPY_Q] > 0.0 && ph[SHARPY_DL] > 0.0 && fabs(ph[SHARPY_SINDEC]) <= 1.0 &&
-           fabs(ph[SHARPY_COSI]) <= 1.0)
-              ? 1
-              : 0;
+  sc.ok = phys_ok(ph) ? 1 : 0;
   if (!sc.ok) {
     sc.kisco = -1;
     return;
@@ -386,7 +393,19 @@ __device__ void prologue(const DevModel& m, const DevEvent& ev, const double* th
 #pragma unroll
     for (int i = 0; i < 4; ++i) ec.dc0[i] = cpn.d[i];
   sc.kisco = isco_bin(ev, fisco);
+  if (SPLIT) {
+#pragma unroll
+    for (int j = 0; j < kNPn; ++j) split2(sc.alpha[j], &sc.ahi[j], &sc.alo[j]);
+    sc.c0f = (float)(sc.c0 - rint(sc.c0));
+  }
+}
 
+template <class DT, bool GRAD, bool SPLIT = false>
+__device__ void prologue_sky(const DevModel& m, const DevEvent& ev, const double* th, SweepCoef& sc,
+                             EpiCoef<DT>& ec) {
+  double ph[SHARPY_NPHYS];
+  to_physical(m, th, ph);
+  if (!phys_ok(ph)) return;
   // Newtonian amplitude of an optimally oriented source: sqrt(5/24) pi^(-2/3) (T Mc)^(5/6) / D
   const DT mc = (DT)ph[SHARPY_MC], dl = (DT)ph[SHARPY_DL];
   ec.A0 = (double)((DT)(0.45643546458763845 * 0.46619407703541166) * pow((DT)kTsun * mc, DT(5.0 / 6.0)) /
@@ -426,12 +445,16 @@ __device__ void prologue(const DevModel& m, const DevEvent& ev, const double* th
       ec.dtau[a][1] = an.ddt[1];
     }
   }
-  if (SPLIT) {
-#pragma unroll
-    for (int j = 0; j < kNPn; ++j) split2(sc.alpha[j], &sc.ahi[j], &sc.alo[j]);
+  if (SPLIT)
     for (int a = 0; a < ev.n_det; ++a) split2(sc.tau[a], &sc.thi[a], &sc.tlo[a]);
-    sc.c0f = (float)(sc.c0 - rint(sc.c0));
-  }
+}
+
+// theta (free dims) -> sweep and epilogue coefficients.
+template <class DT, bool GRAD, bool SPLIT = false>
+__device__ void prologue(const DevModel& m, const DevEvent& ev, const double* th, SweepCoef& sc,
+                         EpiCoef<DT>& ec) {
+  prologue_phase<DT, GRAD, SPLIT>(m, ev, th, sc, ec);
+  prologue_sky<DT, GRAD, SPLIT>(m, ev, th, sc, ec);
 }
 
 // Moments layout: mom[a][j][re/im], j = 0..8 basis (8 = f), j = 9 plain sum Z.
