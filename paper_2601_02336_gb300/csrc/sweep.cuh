@@ -47,34 +47,34 @@ __device__ __forceinline__ int acc_to_mom(int i) {
 // l (NP/32) ... l (NP/32) + NP/32 - 1 in v[0 .. NP/32); for NP < 32 the lanes
 // of each group of 32/NP consecutive lanes all hold the sum of value
 // l / (32/NP) in v[0].
-template <int N, int OFF>
+template <int N, int OFF, class T = float>
 struct ReduceScatter {
-  static __device__ __forceinline__ void run(float* v, int lane) {
+  static __device__ __forceinline__ void run(T* v, int lane) {
     constexpr int H = N / 2;
     const bool up = (lane & OFF) != 0;
 #pragma unroll
     for (int j = 0; j < H; ++j) {
-      const float send = up ? v[j] : v[j + H];
-      const float keep = up ? v[j + H] : v[j];
+      const T send = up ? v[j] : v[j + H];
+      const T keep = up ? v[j + H] : v[j];
       v[j] = keep + __shfl_xor_sync(0xffffffffu, send, OFF);
     }
-    ReduceScatter<H, OFF / 2>::run(v, lane);
+    ReduceScatter<H, OFF / 2, T>::run(v, lane);
   }
 };
-template <int OFF>
-struct ReduceScatter<1, OFF> {
-  static __device__ __forceinline__ void run(float* v, int) {
+template <int OFF, class T>
+struct ReduceScatter<1, OFF, T> {
+  static __device__ __forceinline__ void run(T* v, int) {
 #pragma unroll
     for (int o = OFF; o >= 1; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
   }
 };
-template <int N>
-struct ReduceScatter<N, 0> {
-  static __device__ __forceinline__ void run(float*, int) {}
+template <int N, class T>
+struct ReduceScatter<N, 0, T> {
+  static __device__ __forceinline__ void run(T*, int) {}
 };
-template <>
-struct ReduceScatter<1, 0> {
-  static __device__ __forceinline__ void run(float*, int) {}
+template <class T>
+struct ReduceScatter<1, 0, T> {
+  static __device__ __forceinline__ void run(T*, int) {}
 };
 
 template <int NACC>
@@ -281,10 +281,19 @@ __device__ void sweep_fp64(const DevEvent& ev, const SweepCoef& sc, double* mom)
       }
     }
   }
+  // warp reduce-scatter (the same pairing as a butterfly sum per moment, with
+  // NP/2 + NP/4 + ... FP64 adds per lane instead of 5 NP)
+  using F = FlushShape<NACC>;
+  double v[F::NP];
 #pragma unroll
-  for (int i = 0; i < NACC; ++i) {
-    double v = warp_sum(acc[i]);
-    if (lane == 0) mom[acc_to_mom<NDET, GRAD>(i)] = v;
+  for (int i = 0; i < F::NP; ++i) v[i] = i < NACC ? acc[i] : 0.0;
+  ReduceScatter<F::NP, 16, double>::run(v, lane);
+  if (F::owner(lane)) {
+#pragma unroll
+    for (int t = 0; t < F::KEEP; ++t) {
+      const int idx = F::index(lane, t);
+      if (idx < NACC) mom[acc_to_mom<NDET, GRAD>(idx)] = v[t];
+    }
   }
 }
 

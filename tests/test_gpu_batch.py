@@ -56,6 +56,23 @@ def test_batch_matches_separate_runs(precision):
     assert b.launches == 1 + 2 * len(ws) + 7 * rounds2
 
 
+@pytest.mark.parametrize("slots", [8, 32])
+def test_batch_forced_slots_match_separate_runs(slots):
+    """The batched NUTS launch with a forced slot count (32: many sweeps per CTA, each warp runs whole
+    particles; 8: few, the warps share each particle) against separate runs, bit for bit: a particle's
+    trajectory must not depend on how its CTA schedules the sweeps."""
+    G.require_gpu()
+    ws = _uneven_events()
+    ctxs = [api.make_event(w, seed=10 + i)[0] for i, w in enumerate(ws)]
+    keys = [21, 22, 23]
+    kw = dict(alpha=0.5, n_mut=2, max_depth=6, metric=0, eps_scale=0.5, precision="mixed", max_stages=200)
+    b = api.Batch(ctxs, [w.n_particles for w in ws], **kw)
+    b.slots = slots
+    res, _ = b.run(keys)
+    assert b.slots == slots
+    _check_against_runs(b, ws, ctxs, keys, res, **kw)
+
+
 @pytest.mark.parametrize("metric", [1, 2])
 def test_batch_dense_metrics_single_detector(metric):
     """Two single-detector events (different noise) with the weighted-covariance metric (1) and the

@@ -100,9 +100,13 @@ def test_nuts_taylorf2_11d_mixed_vs_fp64(precision):
     dev = np.max(np.abs(out["fp64"][0] - out[precision][0]) / G.width(w)[None, :], axis=1)
     assert np.mean(dev < 1e-6) >= 0.8
     assert np.all(np.isfinite(out[precision][0]))
-    # self-consistency of the outputs
-    l2, _ = ctx.loglike_grad(G.to_dev(out[precision][0]), precision)
-    assert np.allclose(l2.cpu().numpy(), out[precision][1], rtol=0, atol=1e-6)
+    # the returned ln L belongs to the returned theta: against the FP64 value within the mixed tolerance, and
+    # against the standalone mixed call (the same sweep code) to rounding
+    th_m = G.to_dev(out[precision][0])
+    l64, _ = ctx.loglike_grad(th_m, "fp64")
+    l2, _ = ctx.loglike_grad(th_m, precision)
+    assert np.max(np.abs(l64.cpu().numpy() - out[precision][1])) <= 1e-3
+    assert np.max(np.abs(l2.cpu().numpy() - out[precision][1])) <= 1e-6
     assert ctx.status() == 0
 
 
