@@ -151,7 +151,10 @@ void sharpy_destroy(sharpy_ctx* ctx);
    psd[n_det][n_bins], both HOST arrays, copied (the caller keeps ownership).
    Builds the noise weights w = 4 df / S, the pre-whitened data, the basis and
    prefix tables and <d|d>. Synchronous. SHARPY_ENONFINITE if d or the PSD has
-   a NaN/Inf or the PSD is not positive. */
+   a NaN/Inf or the PSD is not positive. A call for a new event on the same
+   grid and detector count keeps the grid tables and device buffers (it waits
+   for the device, then rebuilds and copies only the data-dependent tables);
+   the local-metric tables are kept while the PSD is unchanged. */
 int sharpy_set_data(sharpy_ctx* ctx, int n_det, int64_t n_bins, double f_min, double df,
                     const double* d_re_im, const double* psd, const sharpy_detector* det);
 

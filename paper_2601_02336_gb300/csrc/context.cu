@@ -166,20 +166,58 @@ int sharpy_set_data(sharpy_ctx* c, int n_det, int64_t n_bins, double f_min, doub
   int rc = check_ctx(c, false);
   if (rc) return rc;
 
-  std::vector<double> f(K), b64(kNBasis * K), e64(2 * n_det * K), pref(n_det * K), wamp2(n_det * K);
-  std::vector<float> b32(kNBasis * K), b32lo(kNBasis * K), e32(2 * n_det * K);
-  for (int64_t k = 0; k < K; ++k) {
-    double fk = f_min + (double)k * df;
-    f[k] = fk;
-    double x = std::cbrt(1.0 / fk), y = std::cbrt(fk), l = std::log(fk);
-    double x2 = x * x;
-    double B[kNBasis] = {x2 * x2 * x, x2 * x, x2, x, l, y, y * l, y * y, fk};
-    for (int j = 0; j < kNBasis; ++j) {
-      b64[j * K + k] = B[j];
-      b32[j * K + k] = (float)B[j];
-      b32lo[j * K + k] = (float)(B[j] - (double)b32[j * K + k]);
+  // The frequency-grid tables (f, basis functions, f^-7/6) depend only on
+  // (K, f_min, df): a new event on the same grid and detector count keeps
+  // them and the device buffers, and only the data-dependent tables are
+  // rebuilt and copied.
+  const bool same_grid = c->has_data && c->ev.n_det == n_det && c->ev.n_bins == K && c->ev.f_min == f_min &&
+                         c->ev.df == df && (int64_t)c->h_amp.size() == K;
+  if (!same_grid) {
+    std::vector<double> f(K), b64(kNBasis * K), amp(K);
+    std::vector<float> b32(kNBasis * K), b32lo(kNBasis * K);
+    for (int64_t k = 0; k < K; ++k) {
+      double fk = f_min + (double)k * df;
+      f[k] = fk;
+      double x = std::cbrt(1.0 / fk), y = std::cbrt(fk), l = std::log(fk);
+      double x2 = x * x;
+      double B[kNBasis] = {x2 * x2 * x, x2 * x, x2, x, l, y, y * l, y * y, fk};
+      for (int j = 0; j < kNBasis; ++j) {
+        b64[j * K + k] = B[j];
+        b32[j * K + k] = (float)B[j];
+        b32lo[j * K + k] = (float)(B[j] - (double)b32[j * K + k]);
+      }
+      amp[k] = std::pow(fk, -7.0 / 6.0);
     }
+    free_event(c);
+    bool ok = cudaMalloc(&c->d_f, K * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&c->d_b64, kNBasis * K * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&c->d_b32, kNBasis * K * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&c->d_b32lo, kNBasis * K * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&c->d_e64, n_det * K * sizeof(double2)) == cudaSuccess &&
+              cudaMalloc(&c->d_e32, n_det * K * sizeof(float2)) == cudaSuccess &&
+              cudaMalloc(&c->d_pref, n_det * K * sizeof(double)) == cudaSuccess;
+    if (!ok) {
+      free_event(c);
+      return SHARPY_ENOMEM;
+    }
+    ok = cudaMemcpy(c->d_f, f.data(), K * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(c->d_b64, b64.data(), b64.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(c->d_b32, b32.data(), b32.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(c->d_b32lo, b32lo.data(), b32lo.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+      free_event(c);
+      return SHARPY_ECUDA;
+    }
+    c->h_basis.swap(b64);
+    c->h_amp.swap(amp);
+    c->h_wamp2.clear();
+  } else if (cudaDeviceSynchronize() != cudaSuccess) {
+    // the previous event's tables may still be read by queued work
+    return SHARPY_ECUDA;
   }
+  const std::vector<double>& amp = c->h_amp;
+  std::vector<double> e64(2 * n_det * K), pref(n_det * K), wamp2(n_det * K);
+  std::vector<float> e32(2 * n_det * K);
   // <d|d> with a compensated sum; P_a prefix sums of w f^-7/3 (compensated).
   double dd = 0.0, ddc = 0.0;
   for (int a = 0; a < n_det; ++a) {
@@ -188,13 +226,12 @@ int sharpy_set_data(sharpy_ctx* c, int n_det, int64_t n_bins, double f_min, doub
       int64_t i = a * K + k;
       double w = 4.0 * df / psd[i];
       double dr = d[2 * i], di = d[2 * i + 1];
-      double amp = std::pow(f[k], -7.0 / 6.0);
       // E = w conj(d) f^-7/6
-      e64[2 * i] = w * dr * amp;
-      e64[2 * i + 1] = -w * di * amp;
+      e64[2 * i] = w * dr * amp[k];
+      e64[2 * i + 1] = -w * di * amp[k];
       e32[2 * i] = (float)e64[2 * i];
       e32[2 * i + 1] = (float)e64[2 * i + 1];
-      double term = w * amp * amp;
+      double term = w * amp[k] * amp[k];
       wamp2[i] = term;
       double t = s + term;
       cmp += std::fabs(s) >= std::fabs(term) ? (s - t) + term : (term - t) + s;
@@ -206,28 +243,19 @@ int sharpy_set_data(sharpy_ctx* c, int n_det, int64_t n_bins, double f_min, doub
       dd = u;
     }
   }
-  free_event(c);
-  bool ok = cudaMalloc(&c->d_f, K * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&c->d_b64, kNBasis * K * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&c->d_b32, kNBasis * K * sizeof(float)) == cudaSuccess &&
-            cudaMalloc(&c->d_b32lo, kNBasis * K * sizeof(float)) == cudaSuccess &&
-            cudaMalloc(&c->d_e64, n_det * K * sizeof(double2)) == cudaSuccess &&
-            cudaMalloc(&c->d_e32, n_det * K * sizeof(float2)) == cudaSuccess &&
-            cudaMalloc(&c->d_pref, n_det * K * sizeof(double)) == cudaSuccess;
-  if (!ok) {
-    free_event(c);
-    return SHARPY_ENOMEM;
-  }
-  ok = cudaMemcpy(c->d_f, f.data(), K * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
-       cudaMemcpy(c->d_b64, b64.data(), b64.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
-       cudaMemcpy(c->d_b32, b32.data(), b32.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
-       cudaMemcpy(c->d_b32lo, b32lo.data(), b32lo.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
-       cudaMemcpy(c->d_e64, e64.data(), e64.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
-       cudaMemcpy(c->d_e32, e32.data(), e32.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
-       cudaMemcpy(c->d_pref, pref.data(), pref.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+  const bool ok = cudaMemcpy(c->d_e64, e64.data(), e64.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(c->d_e32, e32.data(), e32.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(c->d_pref, pref.data(), pref.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
   if (!ok) {
     free_event(c);
     return SHARPY_ECUDA;
+  }
+  // the Fisher prefix tables depend on w f^-7/3 only: kept while it is unchanged
+  if (wamp2 != c->h_wamp2) {
+    cudaFree(c->d_p1);
+    cudaFree(c->d_p2);
+    c->d_p1 = c->d_p2 = nullptr;
+    c->h_wamp2.swap(wamp2);
   }
   DevEvent& ev = c->ev;
   ev.n_det = n_det;
@@ -243,11 +271,9 @@ int sharpy_set_data(sharpy_ctx* c, int n_det, int64_t n_bins, double f_min, doub
   ev.e64 = c->d_e64;
   ev.e32 = c->d_e32;
   ev.pref = c->d_pref;
-  ev.p1 = nullptr;
-  ev.p2 = nullptr;
+  ev.p1 = c->d_p1;
+  ev.p2 = c->d_p2;
   for (int a = 0; a < n_det; ++a) detector_geometry(det[a], ev.det[a]);
-  c->h_wamp2.swap(wamp2);
-  c->h_basis.swap(b64);
   c->has_data = true;
   return SHARPY_OK;
 }

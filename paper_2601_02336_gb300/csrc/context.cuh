@@ -31,6 +31,7 @@ struct sharpy_ctx {
   // host copies for the Fisher-information prefix tables (built on first use)
   std::vector<double> h_wamp2;  // [n_det][K] w f^-7/3
   std::vector<double> h_basis;  // [kNBasis][K]
+  std::vector<double> h_amp;    // [K] f^-7/6 (grid table kept for the next event on the same grid)
   double* d_p1 = nullptr;       // [n_det][kNBasis][K] prefix sums of w f^-7/3 B_m
   double* d_p2 = nullptr;       // [n_det][kNBasis (kNBasis + 1) / 2][K] prefix sums of w f^-7/3 B_m B_n
   // NUTS slot count picked by the autotuner for (tuned_n, tuned_prec)

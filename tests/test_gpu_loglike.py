@@ -175,6 +175,31 @@ def test_set_data_rejects_nonfinite():
         ctx.loglike_grad(G.to_dev(inputs.prior_draws(w, 2, 1)))
 
 
+def test_set_data_again_on_the_same_grid():
+    """A second event on the same grid reuses the grid tables: its likelihood, gradient and local metric are
+    bit-identical to a fresh context's, also when the PSD changes (the metric tables are rebuilt then)."""
+    G.require_gpu()
+    w = inputs.bbh11()
+    dets = inputs.detectors(w)
+    psd = inputs.psd_array(w)
+    _, _, d0 = helpers.make_event(w, seed=0)
+    _, _, d1 = helpers.make_event(w, seed=1)
+    th = G.to_dev(inputs.prior_draws(w, 64, 7))
+    ctx = api.Context.from_workload(w)
+    ctx.set_data(d0, psd, w.f_min, w.df, dets)
+    ctx.loglike_grad(th, "mixed")
+    ctx.local_metric(th, 0.5, want=("mass",))
+    for data, p in ((d1, psd), (d1, psd * 1.5)):
+        ctx.set_data(data, p, w.f_min, w.df, dets)
+        fresh = api.Context.from_workload(w)
+        fresh.set_data(data, p, w.f_min, w.df, dets)
+        for prec in ("fp64", "mixed", "split"):
+            a, b = ctx.loglike_grad(th, prec), fresh.loglike_grad(th, prec)
+            assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]), prec
+        ma, mb = ctx.local_metric(th, 0.5, want=("mass",)), fresh.local_metric(th, 0.5, want=("mass",))
+        assert torch.equal(ma["mass"], mb["mass"])
+
+
 def test_autograd_backward_is_the_adjoint():
     G.require_gpu()
     w = inputs.bbh11()
