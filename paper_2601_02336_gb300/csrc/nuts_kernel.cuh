@@ -13,14 +13,15 @@
 //      (responses, delays, amplitude) on its neighbour, a warp on another SM
 //      sub-partition;
 //   B  each warp sweeps the bins of the next pending particle, longest first;
-//   C  lane l < SLOTS/kNutsWarps of warp w owns slot w SLOTS/kNutsWarps + l:
-//      the epilogue, the tree update and the first half of the next leapfrog.
+//   C  each pending slot's epilogue, tree update and first half of the next
+//      leapfrog, on a lane group of 32/(SLOTS/4) lanes (one or more dimensions
+//      per lane), the pending slots dealt out one per warp first.
 // An FP64 warp instruction costs the same pipe time whatever its active-lane
 // count, and a warp runs the union of its lanes' branches of the state
 // machine: spreading both over the sub-partitions shortens the serial part of
 // a tick. Particles with shallow trees finish early and leave their slot idle;
-// the tree state of every slot lives in shared memory ([field][dim][slot],
-// conflict-free across lanes).
+// the tree state of every slot lives in shared memory ([field][slot][dim]: a
+// slot's lane group reads consecutive words).
 //
 // Precision of the tree state (template VT): positions theta and the potential
 // energy are FP64 on every path. The FP64 path keeps momenta, velocities,
@@ -94,6 +95,27 @@ struct NutsArgs {
 
 enum { METRIC_IDENTITY = 0, METRIC_DIAGONAL = 1, METRIC_DENSE = 2 };
 
+// Per-slot state machine scalars: kept in shared memory between ticks and in
+// the registers of the lane group that advances the slot in a tick (identical
+// in all its lanes).
+template <class VT>
+struct Slot {
+  int64_t pid;
+  int t;           // transition index
+  int depth;       // completed doublings
+  long n;          // leaf index within the current sub-tree
+  int dir;
+  uint32_t leaf_ctr;
+  double h0;       // Hamiltonian at the start of the transition
+  double lnl_p, lnl_s, lnl_new;
+  VT logw, logw_sub, acc;
+  int n_leaf, divergent;
+  int done;
+  // stats
+  double st_acc, st_bins;
+  int st_depth, st_leap, st_div;
+};
+
 template <int SLOTS, class VT>
 struct NutsShared {
   double pos[P_COUNT][SLOTS][kMaxDim];  // [field][slot][dim]: a slot's lanes read consecutive words
@@ -113,6 +135,8 @@ struct NutsShared {
   int order[SLOTS];  // this tick's sweeps, longest (largest k_ISCO) first
   int n_order;
   int next;          // next entry of order to claim
+  int cslot[SLOTS];  // this tick's state machine of lane group g: slot cslot[g], or -1
+  Slot<VT> sstate[SLOTS];
 };
 
 // Elementary functions in the state machine's precision.
@@ -153,26 +177,6 @@ __device__ __forceinline__ void draw2(uint64_t key, uint32_t c0, uint32_t c1, ui
   *u0 = ((float)(x[0] >> 8) + 0.5f) * 5.9604644775390625e-8f;  // 2^-24
   *u1 = ((float)(x[2] >> 8) + 0.5f) * 5.9604644775390625e-8f;
 }
-
-// Per-slot state machine: the scalars live in registers, identical in every
-// lane of the slot's lane group.
-template <class VT>
-struct Slot {
-  int64_t pid;
-  int t;           // transition index
-  int depth;       // completed doublings
-  long n;          // leaf index within the current sub-tree
-  int dir;
-  uint32_t leaf_ctr;
-  double h0;       // Hamiltonian at the start of the transition
-  double lnl_p, lnl_s, lnl_new;
-  VT logw, logw_sub, acc;
-  int n_leaf, divergent;
-  int done;
-  // stats
-  double st_acc, st_bins;
-  int st_depth, st_leap, st_div;
-};
 
 // Lanes per slot and dimensions per lane of the state machine: a slot's G
 // lanes each own the dimensions t, t + G, ... (t < G) of its vectors, padded
@@ -710,8 +714,8 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(const __grid_c
   const int my = warp * SPW + lane / G;  // this lane's slot
   const int tg = lane % G;                // its lane within the slot's group
   const unsigned gmask = (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << (lane - tg);
-  Slot<VT> sl;
   {
+    Slot<VT> sl;
     NT nu(A, S, my, tg, gmask);
     sl.pid = (int64_t)s_block * SLOTS + my;
     sl.t = 0;
@@ -740,7 +744,10 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(const __grid_c
       sl.done = 0;
       active = nu.advance(sl, false, nullptr, 0.0, nullptr);
     }
-    if (tg == 0) S.pending[my] = active ? 1 : 0;
+    if (tg == 0) {
+      S.pending[my] = active ? 1 : 0;
+      S.sstate[my] = sl;
+    }
   }
   __syncthreads();
   const long max_ticks = (long)A.n_steps * ((1L << A.max_depth) + 1) + 4;
@@ -783,6 +790,18 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(const __grid_c
         S.next = 0;
       }
     }
+    if (warp == cw) {
+      // this tick's state machines, one per warp before a second one on any
+      // warp: pending slot of rank i goes to group (i mod 4) SPW + i / 4
+      const bool pd = lane < SLOTS && S.pending[lane];
+      const unsigned pm = __ballot_sync(0xffffffffu, pd);
+      if (lane < SLOTS) S.cslot[lane] = -1;
+      __syncwarp();
+      if (pd) {
+        const int r = __popc(pm & ((1u << lane) - 1u));
+        S.cslot[(r % kNutsWarps) * SPW + r / kNutsWarps] = lane;
+      }
+    }
     __syncthreads();
     // (B) sweeps: each warp claims the next sweep of the longest-first order
     // (a sweep writes all its moments; the warp that runs it does not change
@@ -799,10 +818,13 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(const __grid_c
     }
     __syncthreads();
     // (C) epilogues (or direct evaluations: Gaussian mixture) and state
-    // machines, each on its slot's lane group (the scalar parts run
-    // identically on every lane of the group)
-    if (S.pending[my]) {
-      NT nu(A, S, my, tg, gmask);
+    // machines, each on the lane group assigned to it this tick (the scalar
+    // parts run identically on every lane of the group); which group runs a
+    // slot does not change what it computes
+    const int cs = S.cslot[warp * SPW + lane / G];
+    if (cs >= 0) {
+      Slot<VT> sl = S.sstate[cs];
+      NT nu(A, S, cs, tg, gmask);
       VT gl_new[DPL], glp_new[DPL];
       double x[DPL];
 #pragma unroll
@@ -810,13 +832,13 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(const __grid_c
       if (gw) {
         DT gph[SHARPY_NPHYS];
         sl.lnl_new = NAN;
-        if (sc[my].ok) {
-          epilogue<DT, true>(A.ev, sc[my], ec[my], mom[my], &sl.lnl_new, gph);
-          sl.st_bins += (double)(sc[my].kisco + 1) * A.ev.n_det;
+        if (sc[cs].ok) {
+          epilogue<DT, true>(A.ev, sc[cs], ec[cs], mom[cs], &sl.lnl_new, gph);
+          sl.st_bins += (double)(sc[cs].kisco + 1) * A.ev.n_det;
         }
 #pragma unroll
         for (int k = 0; k < DPL; ++k)
-          gl_new[k] = !nu.has(k) ? VT(0) : sc[my].ok ? (VT)gph[A.m.phys[nu.dim(k)]] : (VT)NAN;
+          gl_new[k] = !nu.has(k) ? VT(0) : sc[cs].ok ? (VT)gph[A.m.phys[nu.dim(k)]] : (VT)NAN;
       } else {
         double xa[kMaxDim], g[kMaxDim];
         for (int i = 0; i < D; ++i) xa[i] = nu.X(P_N, i);
@@ -830,11 +852,16 @@ __global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(const __grid_c
       for (int k = 0; k < DPL; ++k)
         if (!isfinite(gl_new[k])) gl_new[k] = VT(0);
       const bool more = nu.advance(sl, true, gl_new, lp_new, glp_new);
-      if (tg == 0) S.pending[my] = more ? 1 : 0;
+      nu.sync();
+      if (tg == 0) {
+        S.pending[cs] = more ? 1 : 0;
+        S.sstate[cs] = sl;
+      }
     }
     __syncthreads();  // the control warp reads every slot's pending flag next
   }
   // write back
+  const Slot<VT> sl = S.sstate[my];
   if (sl.pid < A.n) {
     NT nu(A, S, my, tg, gmask);
 #pragma unroll
