@@ -13,20 +13,24 @@
 // moments (the adjoint of the sweep; the paper gets it by autodiff, Sec. 4).
 //
 // Precision (template DT): DT = double is the FP64 path. DT = float is the
-// mixed path: FP64 is kept for what the phase needs to ~1e-12 (the values of
-// alpha, c0 and the delays, k_ISCO) and for the ln L assembly; the antenna
-// patterns, the amplitude, every Jacobian entry and the gradient contraction
-// are FP32 (relative error ~1e-7, far inside the 1e-4 gradient tolerance).
+// mixed path: what the phase needs to ~1e-12 (the values of alpha and c0) is
+// computed in double-float arithmetic (FP32 pairs, ~48 bits; one FP64
+// logarithm) and handed to the sweep as FP64, the delays, k_ISCO and the ln L
+// assembly stay FP64; the antenna patterns, the amplitude, every Jacobian
+// entry and the gradient contraction are FP32 (relative error ~1e-7, far
+// inside the 1e-4 gradient tolerance).
 #pragma once
 #include <type_traits>
 
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace sharpy {
 
-// Value with derivatives along four directions. The value is always FP64;
-// for DT = float an FP32 shadow of the value feeds the derivative arithmetic,
-// so derivatives never need FP64 operations or conversions.
+// Value with derivatives along four directions. The value is FP64 (DT =
+// double) or double-float (DT = float); for DT = float an FP32 shadow of the
+// value feeds the derivative arithmetic, so derivatives need neither FP64
+// operations nor conversions.
 template <class DT>
 struct I4;
 
@@ -40,17 +44,34 @@ struct I4<double> {
 
 template <>
 struct I4<float> {
-  double v;
+  DF v;
   float vf;
   float d[4];
   __device__ __forceinline__ float f() const { return vf; }
   __device__ __forceinline__ void setf(float x) { vf = x; }
 };
 
+// value type of I4<DT>, its FP64 value and its low-precision shadow
+__device__ __forceinline__ double vdbl(double x) { return x; }
+__device__ __forceinline__ double vdbl(DF x) { return df_to_double(x); }
+template <class DT>
+__device__ __forceinline__ DT vlow(double x) { return (DT)x; }
+template <class DT>
+__device__ __forceinline__ DT vlow(DF x) { return x.hi; }
+__device__ __forceinline__ double vrecip(double x) { return 1.0 / x; }
+__device__ __forceinline__ DF vrecip(DF x) { return df_recip(x); }
+template <class DT>
+__device__ __forceinline__ auto vval(double x) {
+  if constexpr (std::is_same<DT, double>::value)
+    return x;
+  else
+    return df_from(x);
+}
+
 template <class DT>
 __device__ __forceinline__ I4<DT> iconst(double x) {
   I4<DT> r;
-  r.v = x;
+  r.v = vval<DT>(x);
   r.setf((DT)x);
 #pragma unroll
   for (int i = 0; i < 4; ++i) r.d[i] = DT(0);
@@ -109,8 +130,8 @@ __device__ __forceinline__ I4<DT> operator+(double s, const I4<DT>& a) {
 template <class DT>
 __device__ __forceinline__ I4<DT> recip(const I4<DT>& a) {
   I4<DT> r;
-  r.v = 1.0 / a.v;
-  r.setf((DT)r.v);
+  r.v = vrecip(a.v);
+  r.setf(vlow<DT>(r.v));
   const DT g = -r.f() * r.f();
 #pragma unroll
   for (int i = 0; i < 4; ++i) r.d[i] = g * a.d[i];
@@ -176,42 +197,40 @@ __device__ __forceinline__ void to_physical(const DevModel& m, const double* th,
 }
 
 // u = (pi Tsun M)^(1/3) = (pi Tsun Mc)^(1/3) eta^(-1/5), 1/u and ln u for the
-// mixed path with one FP64 transcendental instead of three: u = c^(1/15) with
-// c = (pi Tsun Mc)^5 / eta^3. v = 1/u = c^(-1/15) from an FP32 start and two
-// division-free Newton steps v <- v + v (1 - c v^15) / 15 in FP64 (quadratic:
-// 1e-7 -> 1e-13 -> rounding), u = c v^14, ln u = log(u) in FP64 (it sets the
-// constant and 3PN phase terms, which need ~1e-10). Derivatives from
+// mixed path in double-float: u = c^(1/15) with c = (pi Tsun Mc)^5 / eta^3.
+// v = 1/u = c^(-1/15) from an FP32 start and two division-free Newton steps
+// v <- v + v (1 - c v^15) / 15 (quadratic: 1e-7 -> 1e-14 -> rounding),
+// u = c v^14, ln u = log(u) in FP64 (it sets the constant and 3PN phase
+// terms, which need ~1e-10). Derivatives from
 // d ln u = (d Mc / Mc - 3/5 d eta / eta) / 3.
-__device__ __forceinline__ void u_mixed(double mc, const I4<float>& mcv, const I4<float>& eta, const I4<float>& ieta,
+__device__ __forceinline__ void u_mixed(const I4<float>& mcv, const I4<float>& eta, const I4<float>& ieta,
                                         I4<float>& u, I4<float>& ui, I4<float>& lnu) {
-  const double p = (kPi * kTsun) * mc;
-  const double p2 = p * p;
-  const double ie = ieta.v;
-  const double c = (p2 * p2 * p) * (ie * ie * ie);
-  double v = (double)powf((float)c, -1.0f / 15.0f);
+  const DF p = (kPi * kTsun) * mcv.v;
+  const DF p2 = p * p;
+  const DF ie = ieta.v;
+  const DF c = (p2 * p2 * p) * (ie * ie * ie);
+  DF v = {powf(c.hi, -1.0f / 15.0f), 0.0f};
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
-    const double v2 = v * v, v4 = v2 * v2, v8 = v4 * v4;
-    const double v15 = v8 * v4 * v2 * v;
-    v = fma(v * (1.0 / 15.0), fma(-c, v15, 1.0), v);
+    const DF v2 = v * v, v4 = v2 * v2, v8 = v4 * v4;
+    const DF v15 = v8 * v4 * v2 * v;
+    v = v + ((1.0 / 15.0) * v) * (df_from(1.0) - c * v15);
   }
-  const double v2 = v * v, v4 = v2 * v2, v8 = v4 * v4;
-  const double uu = c * (v8 * v4 * v2);
-  const float uf = (float)uu;
-  const double l = log(uu);
-  const float vf = (float)v;
-  lnu.v = l;
+  const DF v2 = v * v, v4 = v2 * v2, v8 = v4 * v4;
+  const DF uu = c * (v8 * v4 * v2);
+  const double l = log(df_to_double(uu));
+  lnu.v = df_from(l);
   lnu.vf = (float)l;
   u.v = uu;
-  u.vf = uf;
+  u.vf = uu.hi;
   ui.v = v;
-  ui.vf = vf;
+  ui.vf = v.hi;
   const float imc = 1.0f / mcv.vf, ieta_f = 1.0f / eta.vf;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     lnu.d[i] = (1.0f / 3.0f) * (mcv.d[i] * imc - 0.6f * eta.d[i] * ieta_f);
-    u.d[i] = uf * lnu.d[i];
-    ui.d[i] = -vf * lnu.d[i];
+    u.d[i] = u.vf * lnu.d[i];
+    ui.d[i] = -ui.vf * lnu.d[i];
   }
 }
 
@@ -239,9 +258,9 @@ __device__ void pn_coefficients(const double* ph, I4<DT>* alpha, I4<DT>& cpn, do
     mtot = u.v * u.v * u.v / (kPi * kTsun);
     fisco = 1.0 / (14.696938456699069 * kPi * kTsun * mtot);  // 6^(3/2) pi M
   } else {
-    u_mixed(ph[SHARPY_MC], mc, eta, ieta, u, ui, lnu);
-    mtot = u.v * u.v * u.v * (1.0 / (kPi * kTsun));
-    fisco = (ui.v * ui.v * ui.v) * (1.0 / 14.696938456699069);  // 1 / (6^(3/2) u^3)
+    u_mixed(mc, eta, ieta, u, ui, lnu);
+    mtot = 0.0;  // not needed: f_ISCO from 1/u directly
+    fisco = df_to_double((1.0 / 14.696938456699069) * (ui.v * ui.v * ui.v));  // 1 / (6^(3/2) u^3)
   }
   const I4<DT> chis = 0.5 * (c1 + c2);
   const I4<DT> chia = 0.5 * (c1 - c2);
@@ -383,12 +402,12 @@ __device__ void prologue_phase(const DevModel& m, const DevEvent& ev, const doub
   pn_coefficients<DT>(ph, alpha, cpn, mtot, fisco);
 #pragma unroll
   for (int j = 0; j < kNPn; ++j) {
-    sc.alpha[j] = alpha[j].v;
+    sc.alpha[j] = vdbl(alpha[j].v);
     if (GRAD)
 #pragma unroll
       for (int i = 0; i < 4; ++i) ec.dalpha[j][i] = alpha[j].d[i];
   }
-  sc.c0 = cpn.v - ph[SHARPY_PHIC] * (1.0 / kTwoPi) - 0.125;
+  sc.c0 = vdbl(cpn.v) - ph[SHARPY_PHIC] * (1.0 / kTwoPi) - 0.125;
   if (GRAD)
 #pragma unroll
     for (int i = 0; i < 4; ++i) ec.dc0[i] = cpn.d[i];
