@@ -42,13 +42,14 @@ UNIT = "evals/s"
 # fp64: phase as mixed, carrier by sincospi (~30 FMA) and moments in FP64.
 def work(precision, n_det=3):
     """Algorithmic FLOP per active (bin, detector) of the gradient sweep with n_det detectors."""
-    phase64 = 2.0 * (8.0 / n_det + 1.0)          # FP64 FMA: 8 per bin shared by the detectors + 1 per detector
-    phase32 = 8.0 * 13.5 / n_det + 15.0          # split FP32 phase: 8 split products per bin + per-detector part
+    poly64 = 2.0 * 8.0 / n_det                   # FP64 FMA: the 8-term PN polynomial, once per bin for all detectors
+    delay32 = 15.0                               # FP32: f tau_a from hi/lo splits, per detector
+    phase32 = 8.0 * 13.5 / n_det + delay32       # split FP32 phase: 8 split products per bin + the delay term
     if precision == "mixed":
-        return {"pipe": "fp64", "flop": phase64, "fp32_flop": 45.0}
+        return {"pipe": "fp64", "flop": poly64, "fp32_flop": delay32 + 45.0}
     if precision == "split":
         return {"pipe": "fp32", "flop": phase32 + 45.0, "fp32_flop": phase32 + 45.0}
-    return {"pipe": "fp64", "flop": phase64 + 60.0 + 45.0, "fp32_flop": 0.0}
+    return {"pipe": "fp64", "flop": poly64 + 2.0 + 60.0 + 45.0, "fp32_flop": 0.0}
 
 
 WORK = {p: work(p) for p in ("mixed", "split", "fp64")}

@@ -166,7 +166,7 @@ struct SweepCoef {
   double tau[kMaxDet];  // t_c + delay_a [s]
   // split single-precision copies (SHARPY_MIXED_SPLIT): x = hi + lo to ~48 bits
   float ahi[kNPn], alo[kNPn];
-  float thi[kMaxDet], tlo[kMaxDet];
+  float thi[kMaxDet], tlo[kMaxDet];  // (also the mixed path's delays)
   float c0f;            // c0 reduced to [-1/2, 1/2] turns
   int kisco;            // last bin with f_k <= f_ISCO (-1: none)
   int ok;               // 0 if the parameters are outside the model's domain
@@ -464,7 +464,8 @@ __device__ void prologue_sky(const DevModel& m, const DevEvent& ev, const double
       ec.dtau[a][1] = an.ddt[1];
     }
   }
-  if (SPLIT)
+  // hi/lo of the delays: the split and the mixed sweeps form f tau_a in FP32
+  if (SPLIT || std::is_same<DT, float>::value)
     for (int a = 0; a < ev.n_det; ++a) split2(sc.tau[a], &sc.thi[a], &sc.tlo[a]);
 }
 

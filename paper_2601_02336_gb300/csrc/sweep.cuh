@@ -12,12 +12,15 @@
 //                  each product's integer turns are removed exactly (FMA error
 //                  term kept), the fraction stays in [-1/2, 1/2]; no FP64 in
 //                  the bin loop (worst-case phase error ~3e-7 turns).
-//   SHARPY_MIXED : FP64 phase accumulated on top of the offset 1.5 * 2^20
-//                  turns, whose low mantissa word is the fractional turn in
-//                  2^-32 units; FP32 sincos, carrier and moments. Per-lane
-//                  FP32 partial sums are flushed every kFlush iterations
-//                  through a fixed-order warp tree into compensated FP32
-//                  outer accumulators (blocked pairwise summation).
+//   SHARPY_MIXED : the post-Newtonian polynomial accumulated in FP64 on top
+//                  of the offset 1.5 * 2^20 turns, whose low mantissa word is
+//                  its fractional turn in 2^-32 units; the delay term f tau_a
+//                  of each detector in FP32 from hi/lo splits (exact FMA error
+//                  term, fraction added in 32-bit fixed point); FP32 sincos,
+//                  carrier and moments. Per-lane FP32 partial sums are flushed
+//                  every kFlush iterations through a fixed-order warp tree
+//                  into compensated FP32 outer accumulators (blocked pairwise
+//                  summation).
 #pragma once
 #include "physics.cuh"
 
@@ -130,9 +133,6 @@ __device__ void sweep_mixed(const DevEvent& ev, const SweepCoef& sc, float* mom)
   double al[kNPn];
 #pragma unroll
   for (int j = 0; j < kNPn; ++j) al[j] = sc.alpha[j];
-  double tau[NDET];
-#pragma unroll
-  for (int a = 0; a < NDET; ++a) tau[a] = sc.tau[a];
   const double s0 = sc.c0 + kTurnOffset;
   float ah[kNPn], alo[kNPn], th[NDET], tl[NDET];
   if (SPLIT) {
@@ -141,11 +141,11 @@ __device__ void sweep_mixed(const DevEvent& ev, const SweepCoef& sc, float* mom)
       ah[j] = sc.ahi[j];
       alo[j] = sc.alo[j];
     }
+  }
 #pragma unroll
-    for (int a = 0; a < NDET; ++a) {
-      th[a] = sc.thi[a];
-      tl[a] = sc.tlo[a];
-    }
+  for (int a = 0; a < NDET; ++a) {
+    th[a] = sc.thi[a];
+    tl[a] = sc.tlo[a];
   }
   const int kend = sc.kisco;
   int it = 0;
@@ -157,14 +157,18 @@ __device__ void sweep_mixed(const DevEvent& ev, const SweepCoef& sc, float* mom)
     if (GRAD || SPLIT) {
 #pragma unroll
       for (int j = 0; j < kNBasis; ++j) bf[j] = __ldg(ev.b32 + (int64_t)j * K + k);
+    } else {
+      bf[8] = __ldg(ev.b32 + (int64_t)8 * K + k);
     }
+    const float fl = __ldg(ev.b32lo + (int64_t)8 * K + k);
     // phase: FP64 accumulation on the turn offset, or split single precision
-    double S = s0, f = 0.0;
+    double S = s0;
+    int turn_s = 0;
     float F = 0.0f, Sm = 0.0f;
     if (!SPLIT) {
 #pragma unroll
       for (int j = 0; j < kNPn; ++j) S = fma(al[j], __ldg(ev.b64 + (int64_t)j * K + k), S);
-      f = __ldg(ev.b64 + (int64_t)8 * K + k);
+      turn_s = __double2loint(S);  // fractional turn of the polynomial, 2^-32 units
     } else {
       // sum_j alpha_j B_j mod 1: p = ahi*bhi is exact up to e (FMA), its integer
       // part is removed exactly; the fractions are summed pairwise, reduced to
@@ -190,11 +194,14 @@ __device__ void sweep_mixed(const DevEvent& ev, const SweepCoef& sc, float* mom)
     for (int a = 0; a < NDET; ++a) {
       float ang;
       if (!SPLIT) {
-        const double P = fma(f, tau[a], S);
-        const int turn = __double2loint(P);  // fractional turn, 2^-32 units
+        // f tau_a mod 1 from (thi + tlo)(fhi + flo): p = thi fhi is exact up
+        // to e (FMA), the other products are below 2^-20 turn
+        const float p = __fmul_rn(th[a], bf[8]);
+        const float e = fmaf(th[a], fl, fmaf(tl[a], bf[8], fmaf(th[a], bf[8], -p)));
+        const float q = frac_turn(__fadd_rn(frac_turn(p), e));  // [-1/2, 1/2] turn
+        const int turn = turn_s + __float2int_rn(q * 4294967296.0f);  // wraps mod 1 turn
         ang = (float)turn * 1.46291807926715968e-9f;  // 2 pi / 2^32
       } else {
-        const float fl = __ldg(ev.b32lo + (int64_t)8 * K + k);
         const float p = __fmul_rn(th[a], bf[8]);
         float Sa = Sm + fmaf(th[a], bf[8], -p);
         Sa = fmaf(th[a], fl, fmaf(tl[a], bf[8], Sa));
