@@ -47,7 +47,7 @@ enum {
 /* Arithmetic of the likelihood sweep. */
 enum {
   SHARPY_FP64 = 0,  /* every per-bin operation in FP64                                     */
-  SHARPY_MIXED = 1, /* FP64 phase, FP32 carrier and inner products, FP64 reductions/epilogue */
+  SHARPY_MIXED = 1, /* FP64 PN phase polynomial, FP32 delay term, carrier, inner products  */
   SHARPY_MIXED_SPLIT = 2 /* phase in split single precision (no FP64 in the bin loop), FP32 rest */
 };
 

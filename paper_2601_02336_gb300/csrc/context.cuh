@@ -34,10 +34,10 @@ struct sharpy_ctx {
   std::vector<double> h_amp;    // [K] f^-7/6 (grid table kept for the next event on the same grid)
   double* d_p1 = nullptr;       // [n_det][kNBasis][K] prefix sums of w f^-7/3 B_m
   double* d_p2 = nullptr;       // [n_det][kNBasis (kNBasis + 1) / 2][K] prefix sums of w f^-7/3 B_m B_n
-  // NUTS slot count picked by the autotuner for (tuned_n, tuned_prec)
-  int tuned_slots = 0;
-  int64_t tuned_n = -1;
-  int tuned_prec = -1;
+  // NUTS slot count picked by the autotuner, per precision and metric kind
+  // (shared / per-particle), for tuned_n[p][l] particles (0: not tuned)
+  int tuned_slots[3][2] = {};
+  int64_t tuned_n[3][2] = {{-1, -1}, {-1, -1}, {-1, -1}};
 };
 
 namespace sharpy {

@@ -56,7 +56,8 @@ int enqueue_nuts(sharpy_ctx* c, int64_t n, const double* beta_ptr, double beta, 
   A.ctr = ctr;
   A.stats = stats;
   A.status = c->d_status;
-  if (!slots && c->tuned_slots && c->tuned_n == n && c->tuned_prec == precision) slots = c->tuned_slots;
+  const int lm = pminv ? 1 : 0;
+  if (!slots && c->tuned_slots[precision][lm] && c->tuned_n[precision][lm] == n) slots = c->tuned_slots[precision][lm];
   if (!slots) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);

@@ -79,8 +79,8 @@ extern "C" int sharpy_smc_run(sharpy_ctx* c, const sharpy_smc_options* o, uint64
   c->last_stream = s;
   // run buffers: theta, grad [N][D], lnl [N], stats [N], scalars, cov, record;
   // copies of theta, grad, lnl for the autotuner's trials when it has to run
-  const bool tune = !(c->tuned_slots && c->tuned_n == n && c->tuned_prec == o->precision);
   const bool local = o->metric == 2;  // per-particle metric: [N][D][D] inverse and Cholesky factor
+  const bool tune = !(c->tuned_slots[o->precision][local] && c->tuned_n[o->precision][local] == n);
   size_t bytes = (size_t)n * (2 * D + 1) * sizeof(double) * (tune ? 2 : 1) + (size_t)n * sizeof(sharpy_nuts_stats) +
                  (8 + D * D + kRec) * sizeof(double) + (local ? 2 * (size_t)n * D * D * sizeof(double) : 0);
   char* buf = nullptr;
@@ -152,9 +152,8 @@ extern "C" int sharpy_smc_run(sharpy_ctx* c, const sharpy_smc_options* o, uint64
       for (int i = 0; i < kNumSlotChoices; ++i) cands[i].slots = kSlotChoices[i];
       int best = 0;
       if ((rc = tune_slots(cands, kNumSlotChoices, go, s, &best))) return fail(rc);
-      c->tuned_slots = best;
-      c->tuned_n = n;
-      c->tuned_prec = o->precision;
+      c->tuned_slots[o->precision][local] = best;
+      c->tuned_n[o->precision][local] = n;
     }
     if (o->timing) cudaEventRecord(ev0, s);
     rc = enqueue_nuts(c, n, beta_state, 0.0, th, ll, gr, minv, cov_step, o->eps_scale, o->max_depth, o->n_mut, key,
