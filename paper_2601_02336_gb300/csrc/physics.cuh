@@ -14,8 +14,8 @@
 //
 // Precision (template DT): DT = double is the FP64 path. DT = float is the
 // mixed path: what the phase needs to ~1e-12 (the values of alpha and c0) is
-// computed in double-float arithmetic (FP32 pairs, ~48 bits; one FP64
-// logarithm) and handed to the sweep as FP64, the delays, k_ISCO and the ln L
+// computed in double-float arithmetic (FP32 pairs, ~48 bits, no FP64
+// instruction but the conversions) and handed to the sweep as FP64, the delays, k_ISCO and the ln L
 // assembly stay FP64; the antenna patterns, the amplitude, every Jacobian
 // entry and the gradient contraction are FP32 (relative error ~1e-7, far
 // inside the 1e-4 gradient tolerance).
@@ -200,8 +200,8 @@ __device__ __forceinline__ void to_physical(const DevModel& m, const double* th,
 // mixed path in double-float: u = c^(1/15) with c = (pi Tsun Mc)^5 / eta^3.
 // v = 1/u = c^(-1/15) from an FP32 start and two division-free Newton steps
 // v <- v + v (1 - c v^15) / 15 (quadratic: 1e-7 -> 1e-14 -> rounding),
-// u = c v^14, ln u = log(u) in FP64 (it sets the constant and 3PN phase
-// terms, which need ~1e-10). Derivatives from
+// u = c v^14, ln u by the double-float logarithm (it sets the constant and
+// 3PN phase terms, which need ~1e-10). Derivatives from
 // d ln u = (d Mc / Mc - 3/5 d eta / eta) / 3.
 __device__ __forceinline__ void u_mixed(const I4<float>& mcv, const I4<float>& eta, const I4<float>& ieta,
                                         I4<float>& u, I4<float>& ui, I4<float>& lnu) {
@@ -218,9 +218,9 @@ __device__ __forceinline__ void u_mixed(const I4<float>& mcv, const I4<float>& e
   }
   const DF v2 = v * v, v4 = v2 * v2, v8 = v4 * v4;
   const DF uu = c * (v8 * v4 * v2);
-  const double l = log(df_to_double(uu));
-  lnu.v = df_from(l);
-  lnu.vf = (float)l;
+  const DF l = df_log(uu);
+  lnu.v = l;
+  lnu.vf = l.hi;
   u.v = uu;
   u.vf = uu.hi;
   ui.v = v;
