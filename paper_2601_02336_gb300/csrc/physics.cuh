@@ -480,14 +480,19 @@ __device__ void prologue(const DevModel& m, const DevEvent& ev, const double* th
 // Moments layout: mom[a][j][re/im], j = 0..8 basis (8 = f), j = 9 plain sum Z.
 constexpr int kNMom = kNBasis + 1;
 
-// ln L (FP64) and d lnL / d(physical parameters) from the moments.
+// ln L (FP64 total) and d lnL / d(physical parameters) from the moments.
 // The gradient is contracted on the amplitude-scaled moments A0 Z, A0 Y_j and
 // the scaled prefix sum A0^2 P, which are O(SNR^2) and fit FP32 (the raw moments
-// and prefix sums span ~1e-22..1e43).
+// and prefix sums span ~1e-22..1e43). FP64 path: ln L assembled in FP64 from
+// the raw moments. Mixed paths: from the same scaled FP32 quantities with exact
+// products and double-float sums (the moments are FP32 anyway), so only the
+// scaling A0^2 P and the conversions remain FP64.
 template <class DT, bool GRAD, class MT, class GT>
 __device__ void epilogue(const DevEvent& ev, const SweepCoef& sc, const EpiCoef<DT>& ec, const MT* mom, double* lnl,
                          GT* gph) {
+  constexpr bool kDF = std::is_same<DT, float>::value;
   double acc = -0.5 * ev.dd;
+  DF accf = kDF ? df_from(acc) : DF{0.0f, 0.0f};
   DT g[SHARPY_NPHYS];
 #pragma unroll
   for (int i = 0; i < SHARPY_NPHYS; ++i) g[i] = DT(0);
@@ -495,12 +500,20 @@ __device__ void epilogue(const DevEvent& ev, const SweepCoef& sc, const EpiCoef<
   for (int a = 0; a < ev.n_det; ++a) {
     const MT* M = mom + a * kNMom * 2;
     const double P = sc.kisco >= 0 ? ev.pref[(int64_t)a * ev.n_bins + sc.kisco] : 0.0;
-    const double Gr = ec.A0 * (double)ec.cre[a], Gi = ec.A0 * (double)ec.cim[a];
-    acc += (Gr * (double)M[18] - Gi * (double)M[19]) - 0.5 * (Gr * Gr + Gi * Gi) * P;
-    if (!GRAD) continue;
     const DT cr = ec.cre[a], ci = ec.cim[a];
     const DT ps = (DT)(ec.A0 * ec.A0 * P);             // A0^2 P
     const DT zr = a0 * (DT)M[18], zi = a0 * (DT)M[19];  // A0 Z
+    if constexpr (kDF) {
+      // Re(C A0 Z) - |C|^2 A0^2 P / 2
+      const DF re = df_two_prod(cr, zr) - df_two_prod(ci, zi);
+      const DF c2 = df_two_prod(cr, cr) + df_two_prod(ci, ci);
+      const DF c2p = df_two_prod(c2.hi, 0.5f * ps) + DF{__fmul_rn(c2.lo, 0.5f * ps), 0.0f};
+      accf = accf + (re - c2p);
+    } else {
+      const double Gr = ec.A0 * (double)ec.cre[a], Gi = ec.A0 * (double)ec.cim[a];
+      acc += (Gr * (double)M[18] - Gi * (double)M[19]) - 0.5 * (Gr * Gr + Gi * Gi) * P;
+    }
+    if (!GRAD) continue;
     const DT tp = DT(kTwoPi);
     // Im(C X) for a scaled phase-derivative moment X
     auto imcx = [&](DT xr, DT xi) { return cr * xi + ci * xr; };
@@ -533,7 +546,7 @@ __device__ void epilogue(const DevEvent& ev, const SweepCoef& sc, const EpiCoef<
     g[SHARPY_TC] += tp * imcx(yfr, yfi);
     g[SHARPY_PHIC] += -imcx(zr, zi);
   }
-  *lnl = acc;
+  *lnl = kDF ? df_to_double(accf) : acc;
   if (GRAD)
 #pragma unroll
     for (int i = 0; i < SHARPY_NPHYS; ++i) gph[i] = (GT)g[i];
