@@ -260,22 +260,22 @@ struct Nuts {
   template <bool CHECK = true>
   __device__ double prior(const double* x, VT* g) {
     const DevModel& m = A.m;
-    double p[DPL];
+    VT p[DPL];  // the log terms in the state machine's type (FP32 ones are exact: one is nonzero in practice)
     bool inside = true;
 #pragma unroll
     for (int k = 0; k < DPL; ++k) {
       const int d = dim(k);
       g[k] = VT(0);
-      p[k] = 0.0;
+      p[k] = VT(0);
       if (!has(k)) continue;
       if (CHECK && !(x[k] >= m.lo[d] && x[k] <= m.hi[d])) inside = false;
       if (m.prior[d] == SHARPY_PRIOR_POWER2) {
         const VT xi = (VT)x[k];
-        p[k] = (double)(VT(2) * vlog(xi));
+        p[k] = VT(2) * vlog(xi);
         g[k] = VT(2) / xi;
       }
     }
-    const double lp = S.lp_const + gsum(p);
+    const double lp = S.lp_const + (double)gsum(p);
     if (CHECK) inside = __all_sync(gm, inside);
     return inside ? lp : -INFINITY;
   }
@@ -466,10 +466,16 @@ struct Nuts {
       const double u_new = -S.beta * sl.lnl_new - lp_new;
       VT vn[DPL];
       velocity(F_NR, vn);
-      const double dH = u_new + (double)(VT(0.5) * dot(vn, F_NR)) - sl.h0;
+      // energy error: U_new - H0 in FP64 (the two are ~beta ln L, large and
+      // close), the kinetic part added in the state machine's type
+      VT dH;
+      if constexpr (std::is_same<VT, float>::value)
+        dH = (float)(u_new - sl.h0) + VT(0.5) * dot(vn, F_NR);
+      else
+        dH = u_new + (double)(VT(0.5) * dot(vn, F_NR)) - sl.h0;
       sl.n_leaf += 1;
-      sl.acc += (dH == dH) ? (dH <= 0.0 ? VT(1) : vexp((VT)(-dH))) : VT(0);
-      if (!(dH <= kDivergence)) {
+      sl.acc += (dH == dH) ? (dH <= VT(0) ? VT(1) : vexp(-dH)) : VT(0);
+      if (!(dH <= VT(kDivergence))) {
         sl.divergent = 1;
         end_transition(sl);
         goto next_transition;
@@ -487,7 +493,7 @@ struct Nuts {
           V(fgu, d) = gu[k];
           V(fv, d) = vn[k];
         }
-        const VT lw = (VT)(-dH);
+        const VT lw = -dH;
         const VT lw_new = logaddexp(sl.logw_sub, lw);
         VT u0, u1;
         draw2(A.key, (uint32_t)sl.pid, A.ctr + (uint32_t)sl.t, RNG_LEAF, sl.leaf_ctr++, &u0, &u1);
