@@ -425,10 +425,24 @@ __device__ void prologue_sky(const DevModel& m, const DevEvent& ev, const double
   double ph[SHARPY_NPHYS];
   to_physical(m, th, ph);
   if (!phys_ok(ph)) return;
-  // Newtonian amplitude of an optimally oriented source: sqrt(5/24) pi^(-2/3) (T Mc)^(5/6) / D
+  // Newtonian amplitude of an optimally oriented source: sqrt(5/24) pi^(-2/3) (T Mc)^(5/6) / D.
+  // Its square multiplies <h|h>, so for loud templates its precision sets that
+  // of ln L: the mixed path takes (T Mc)^(5/6) from an FP32 power and one
+  // Newton step on y^6 = x^5 in double-float (1e-7 -> 1e-14).
   const DT mc = (DT)ph[SHARPY_MC], dl = (DT)ph[SHARPY_DL];
-  ec.A0 = (double)((DT)(0.45643546458763845 * 0.46619407703541166) * pow((DT)kTsun * mc, DT(5.0 / 6.0)) /
-                   (dl * (DT)kMpcSec));
+  constexpr double kAmp = 0.45643546458763845 * 0.46619407703541166;
+  if constexpr (std::is_same<DT, double>::value) {
+    ec.A0 = kAmp * pow(kTsun * mc, 5.0 / 6.0) / (dl * kMpcSec);
+  } else {
+    const double x = kTsun * ph[SHARPY_MC];
+    const DF X = df_from(x);
+    const DF X2 = X * X, X5 = (X2 * X2) * X;
+    const DF Y = {powf((float)x, 5.0f / 6.0f), 0.0f};
+    const DF Y3 = (Y * Y) * Y, Y6 = Y3 * Y3;
+    const DF t = X5 * df_recip(Y6) - df_from(1.0);
+    const DF Y1 = Y + Y * ((1.0 / 6.0) * t);
+    ec.A0 = df_to_double((kAmp * Y1) * df_recip(df_from(ph[SHARPY_DL] * kMpcSec)));
+  }
   if (GRAD) {
     ec.rel_mc = DT(5.0 / 6.0) / mc;
     ec.rel_dl = DT(-1) / dl;

@@ -75,6 +75,25 @@ def test_loglike_grad_mixed(name, precision):
     _check(w, ev, ctx, thetas, lambda r: 1e-3 + 0 * r, 1e-4, precision)
 
 
+@pytest.mark.parametrize("name", ["tiny", "bbh11", "bbh11_long"])
+def test_mixed_precision_budget(name):
+    """The reduced-precision paths against the GPU FP64 path on 2048 theta (prior draws and a ball around the
+    injection): a budget well inside the 1e-3 tolerance, so that a loss of precision anywhere in the mixed
+    arithmetic (double-float coefficients, fixed-point delay term, compensated moments) shows up here first."""
+    G.require_gpu()
+    w = inputs.WORKLOADS[name]()
+    ev, ctx, th_inj, _ = G.event_pair(w)
+    t = G.to_dev(_thetas(w, th_inj, 1024, 1024, 90))
+    l64, g64 = ctx.loglike_grad(t, "fp64")
+    for precision, budget in (("mixed", 2.5e-4), ("split", 2.5e-4)):
+        l, g = ctx.loglike_grad(t, precision)
+        dl = torch.max(torch.abs(l - l64)).item()
+        err = np.max(G.grad_rel_err(g.cpu().numpy(), g64.cpu().numpy(), G.width(w)))
+        print(name, precision, "max |dlnL|", dl, "max grad rel", err)
+        assert dl <= budget, (precision, dl)
+        assert err <= 2.5e-5, (precision, err)
+
+
 def test_loglike_long_signal_sampled():
     """259585 bins x 3 detectors at full size (sampled particles): mixed within 1e-2, FP64 tight."""
     G.require_gpu()
