@@ -9,9 +9,9 @@
 // recursion), and every leapfrog needs one likelihood+gradient evaluation.
 // Each "tick" of the CTA has three phases between barriers:
 //   A  the prologue of every pending evaluation, lane = slot: the phase half
-//      (PN coefficients, k_ISCO; FP64) on the control warp, the sky half
-//      (responses, delays, amplitude) on its neighbour, a warp on another SM
-//      sub-partition;
+//      (PN coefficients, k_ISCO; FP64, or double-float on the mixed paths) on
+//      the control warp, the sky half (responses, delays, amplitude) on its
+//      neighbour, a warp on another SM sub-partition;
 //   B  each warp sweeps the bins of the next pending particle, longest first;
 //   C  each pending slot's epilogue, tree update and first half of the next
 //      leapfrog, on a lane group of 32/(SLOTS/4) lanes (one or more dimensions
