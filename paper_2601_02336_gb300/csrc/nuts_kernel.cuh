@@ -612,8 +612,12 @@ struct NutsSmem {
   MT mom[SLOTS][NDET * kNMom * 2];
 };
 
+// Mixed paths: registers for three CTAs per SM (168 a thread, no spills),
+// which the 8- and 16-slot launches can use (9 % on 16384 particles); FP64:
+// two.
 template <int PREC, int NDET, int SLOTS>
-__global__ void __launch_bounds__(kNutsWarps * 32, 2) nuts_kernel(const __grid_constant__ NutsArgs P) {
+__global__ void __launch_bounds__(kNutsWarps * 32, PREC == SHARPY_FP64 ? 2 : 3)
+    nuts_kernel(const __grid_constant__ NutsArgs P) {
   using DT = typename std::conditional<PREC == SHARPY_FP64, double, float>::type;
   using VT = DT;
   using MT = typename MomType<PREC>::type;
