@@ -92,6 +92,7 @@ _SIGS = {
     "ref_normal2": (None, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, _D]),
     "ref_antenna": (None, [_P(Detector), C.c_double, C.c_double, C.c_double, _D, _D, _D]),
     "ref_pn_phase": (C.c_double, [C.c_double] * 5),
+    "ref_pn_phase_dmc": (C.c_double, [C.c_double] * 5),
     "ref_pn_beta": (C.c_double, [C.c_double] * 3),
     "ref_amplitude": (C.c_double, [C.c_double] * 3),
     "ref_f_isco": (C.c_double, [C.c_double] * 2),
@@ -226,6 +227,11 @@ def antenna(det: dict, ra, sin_dec, psi):
 
 def pn_phase(mc, q, chi1, chi2, f):
     return lib().ref_pn_phase(mc, q, chi1, chi2, f)
+
+
+def pn_phase_dmc(mc, q, chi1, chi2, f):
+    """d pn_phase / d mc at fixed q, spins and f (forward-mode dual numbers, no step size)."""
+    return lib().ref_pn_phase_dmc(mc, q, chi1, chi2, f)
 
 
 def pn_beta(q, chi1, chi2):

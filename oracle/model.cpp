@@ -342,6 +342,10 @@ void ref_antenna(const ref_detector* det, double ra, double sin_dec, double psi,
 double ref_pn_phase(double mc, double q, double chi1, double chi2, double f) {
   return pn_phase_t<double>(mc, q, chi1, chi2, f);
 }
+double ref_pn_phase_dmc(double mc, double q, double chi1, double chi2, double f) {
+  DualN<1> m = DualN<1>::variable(mc, 0);
+  return pn_phase_t<DualN<1>>(m, DualN<1>(q), DualN<1>(chi1), DualN<1>(chi2), f).d[0];
+}
 double ref_pn_beta(double q, double chi1, double chi2) {
   double eta = q / ((1 + q) * (1 + q));
   double delta = (1 - q) / (1 + q);

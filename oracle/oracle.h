@@ -133,6 +133,7 @@ void ref_antenna(const ref_detector* det, double ra, double sin_dec, double psi,
 
 /* TaylorF2 pieces, exposed for the closed-form pins. */
 double ref_pn_phase(double mc, double q, double chi1, double chi2, double f);   /* (3/128 eta v^5) sum phi_k v^k */
+double ref_pn_phase_dmc(double mc, double q, double chi1, double chi2, double f); /* d ref_pn_phase / d mc (exact, dual numbers) */
 double ref_pn_beta(double q, double chi1, double chi2);                          /* 1.5PN spin-orbit beta */
 double ref_amplitude(double mc, double dl, double f);                            /* Newtonian |h~| for an optimal source */
 double ref_f_isco(double mc, double q);

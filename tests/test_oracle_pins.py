@@ -72,6 +72,143 @@ def test_1pn_chirp_time_coefficient():
         assert abs(coef - expect) < 2e-2 * expect
 
 
+# Published post-Newtonian pins of the full phase. The stationary-phase relation
+# t(f) = (1/2pi) dPsi/df ties the TaylorF2 phase to the chirp time t(v), a
+# series published in other forms and with other numbers than the phase
+# coefficients: (i) Blanchet's TaylorT2 time series (Living Rev. Relativ. 17, 2
+# (2014), the t(x) expansion of Sec. 9.3 through 3.5PN with its 3PN logarithm),
+# with the 1.5PN spin-orbit and 2PN spin-spin parameters of Poisson & Will
+# (PRD 52, 848 (1995)); (ii) the same series DERIVED here by energy balance,
+# dt/dv = -E'(v)/F(v), from the published binding energy E(x) and flux F(x)
+# (Blanchet 2014, non-spinning to 3.5PN; spin-orbit terms at 1.5PN and 2.5PN of
+# Blanchet, Buonanno & Faye, PRD 74, 104034 (2006), in the S_l, Sigma_l
+# variables). The oracle's t(f) comes from its exact (dual-number) derivative of
+# Psi, using f dPsi/df = M_c dPsi/dM_c (Psi depends on f and M_c only through
+# v^3 ~ M_c f at fixed q). Constant phase terms (the "1" of the 2.5PN factor
+# 1 + 3 ln(v/v_lso), and v_lso) have no effect on t(f): they are degenerate with
+# phi_c.
+
+def _oracle_chirp_time(mc, q, c1, c2, v):
+    """t(f) - t_c of the oracle's phase at the frequency where v = (pi M T_sun f)^(1/3)."""
+    eta = q / (1 + q) ** 2
+    mtot = mc * eta ** -0.6
+    f = v ** 3 / (math.pi * TSUN * mtot)
+    return mc / f * oracle.pn_phase_dmc(mc, q, c1, c2, f) / (2 * math.pi), mtot, eta
+
+
+def _sigma_aligned(q, c1, c2):
+    """2PN spin-spin parameter for aligned black-hole spins from the vector form of Arun, Buonanno,
+    Faye & Ochsner (PRD 79, 104023 (2009), Eq. 6.24 and its self-spin terms; Mikoczi, Vasuth & Gergely
+    2005), with the quadrupole parameter kappa = 1 and L.chi_i = chi_i, chi_1.chi_2 = chi_1 chi_2."""
+    x1, x2 = 1 / (1 + q), q / (1 + q)
+    eta, kappa = x1 * x2, 1.0
+    s = eta * (721.0 / 48.0 * c1 * c2 - 247.0 / 48.0 * c1 * c2)
+    for x, c in ((x1, c1), (x2, c2)):
+        s += (720.0 * kappa - 1.0) / 96.0 * x * x * c * c - (240.0 * kappa - 7.0) / 96.0 * x * x * c * c
+    return s
+
+
+def _taylor_t2_series(eta, beta, sigma, v):
+    """Blanchet's TaylorT2 bracket, t - t_c = -(5 M/(256 eta v^8)) * bracket, non-spinning through
+    3.5PN (x = v^2, ln(16 x) = 2 ln(4 v)), plus Poisson & Will's spin terms: -8/5 (4 pi - beta) v^3
+    and -2 sigma v^4."""
+    pi, ge = math.pi, 0.57721566490153286061
+    t2 = 743.0 / 252.0 + 11.0 / 3.0 * eta
+    t3 = -8.0 / 5.0 * (4.0 * pi - beta)
+    t4 = 3058673.0 / 508032.0 + 5429.0 / 504.0 * eta + 617.0 / 72.0 * eta ** 2 - 2.0 * sigma
+    t5 = -7729.0 / 252.0 * pi + 13.0 / 3.0 * pi * eta
+    t6 = (-10052469856691.0 / 23471078400.0 + 128.0 / 3.0 * pi ** 2 + 6848.0 / 105.0 * ge
+          + (3147553127.0 / 3048192.0 - 451.0 / 12.0 * pi ** 2) * eta - 15211.0 / 1728.0 * eta ** 2
+          + 25565.0 / 1296.0 * eta ** 3 + 3424.0 / 105.0 * math.log(16.0 * v * v))
+    t7 = (-15419335.0 / 127008.0 - 75703.0 / 756.0 * eta + 14809.0 / 378.0 * eta ** 2) * pi
+    return 1 + t2 * v ** 2 + t3 * v ** 3 + t4 * v ** 4 + t5 * v ** 5 + t6 * v ** 6 + t7 * v ** 7
+
+
+def _energy_balance_taus(q, c1, c2):
+    """tau_k(ln v) of t - t_c = -(5 M/(256 eta v^8)) sum_k tau_k v^k, derived from the published
+    E(x) and F(x) by series division and term-by-term integration, exact in rationals, pi, gamma_E,
+    ln 2 and L = ln v. Spin terms are kept through 2.5PN only (the model has none at 3PN and 3.5PN,
+    so products of spin-orbit terms, which start at 3PN, are dropped); E and F here carry no
+    spin-spin terms (those enter through sigma)."""
+    sp = pytest.importorskip("sympy")
+    R, pi, ge = sp.Rational, sp.pi, sp.EulerGamma
+    L, s = sp.Symbol("L"), sp.Symbol("s")  # L = ln v; s marks each spin-orbit factor
+    q, c1, c2 = R(q), R(c1), R(c2)
+    x1, x2 = 1 / (1 + q), q / (1 + q)
+    eta, dm = x1 * x2, x1 - x2
+    sl = s * (x1 ** 2 * c1 + x2 ** 2 * c2)  # S_l / M^2
+    sg = s * (x2 * c2 - x1 * c1)            # Sigma_l / M^2
+    # E = -(eta v^2 / 2) sum e_k v^k
+    e = [1, 0, -R(3, 4) - eta / 12, R(14, 3) * sl + 2 * dm * sg,
+         -R(27, 8) + R(19, 8) * eta - eta ** 2 / 24,
+         (11 - R(61, 9) * eta) * sl + dm * (3 - R(10, 3) * eta) * sg,
+         -R(675, 64) + (R(34445, 576) - 205 * pi ** 2 / 96) * eta - R(155, 96) * eta ** 2 - R(35, 5184) * eta ** 3,
+         0]
+    # F = (32/5) eta^2 v^10 sum f_k v^k, ln(16 x) = 4 ln 2 + 2 L
+    f = [1, 0, -R(1247, 336) - R(35, 12) * eta,
+         4 * pi - 4 * sl - R(5, 4) * dm * sg,
+         -R(44711, 9072) + R(9271, 504) * eta + R(65, 18) * eta ** 2,
+         -(R(8191, 672) + R(583, 24) * eta) * pi + (-R(9, 2) + R(272, 9) * eta) * sl
+         + (-R(13, 16) + R(43, 4) * eta) * dm * sg,
+         R(6643739519, 69854400) + 16 * pi ** 2 / 3 - R(1712, 105) * ge - R(856, 105) * (4 * sp.log(2) + 2 * L)
+         + (-R(134543, 7776) + 41 * pi ** 2 / 48) * eta - R(94403, 3024) * eta ** 2 - R(775, 324) * eta ** 3,
+         (-R(16285, 504) + R(214745, 1728) * eta + R(193385, 3024) * eta ** 2) * pi]
+    de = [R(k + 2, 2) * e[k] for k in range(8)]  # -E'(v) = eta v sum (k+2)/2 e_k v^k
+    inv = [sp.Integer(1)] + [0] * 7               # 1 / sum f_k v^k
+    for k in range(1, 8):
+        inv[k] = sp.expand(-sum(f[j] * inv[k - j] for j in range(1, k + 1)))
+    taus = []
+    for k in range(8):
+        a = sp.expand(sum(de[j] * inv[k - j] for j in range(k + 1)))
+        a = sp.expand(a.coeff(s, 0) + (a.coeff(s, 1) if k <= 5 else 0))
+        b, c, n = a.coeff(L, 0), a.coeff(L, 1), k - 8  # integrate v^(n-1) (b + c L)
+        integral = b / n + c * (L - R(1, n)) / n
+        taus.append(sp.lambdify(L, sp.expand(integral * R(5, 32) / eta * R(-256, 5) * eta)))
+    return taus
+
+
+_PN_CASES = [(1.0, 0.0, 0.0), (0.25, 0.0, 0.0), (0.6, 1 / 3, -0.5), (0.125, 0.9, 0.7), (0.9, -0.8, 0.2)]
+
+
+@pytest.mark.parametrize("q,c1,c2", _PN_CASES)
+def test_chirp_time_published_taylor_t2(q, c1, c2):
+    """The oracle's t(f) equals Blanchet's TaylorT2 series (with Poisson & Will's beta and the
+    vector-form sigma) to 1e-12 relative over v = 0.05..0.6 (20 Hz up past the ISCO of the
+    workloads' masses), at five mass ratios and four spin pairs. The 2.5PN spin-orbit term is
+    pinned by the energy-balance test below."""
+    mc = 20.0
+    x1, x2 = 1 / (1 + q), q / (1 + q)
+    eta = x1 * x2
+    beta_pw = sum((113.0 / 12.0 * x * x + 25.0 / 4.0 * eta) * c for x, c in ((x1, c1), (x2, c2)))
+    sigma = _sigma_aligned(q, c1, c2)
+    # the 2.5PN spin-orbit part of tau_5 (3 gamma / 5) is added from the energy-balance series
+    taus = _energy_balance_taus(q, c1, c2)
+    taus0 = _energy_balance_taus(q, 0.0, 0.0)
+    for v in np.linspace(0.05, 0.6, 30):
+        t_or, mtot, eta_o = _oracle_chirp_time(mc, q, c1, c2, v)
+        so25 = (taus[5](math.log(v)) - taus0[5](math.log(v))) * v ** 5
+        t_pub = -5.0 * mtot * TSUN / (256.0 * eta * v ** 8) * (_taylor_t2_series(eta, beta_pw, sigma, v) + so25)
+        assert abs(t_or / t_pub - 1.0) < 1e-12, (q, c1, c2, v, t_or, t_pub)
+
+
+@pytest.mark.parametrize("q,c1,c2", _PN_CASES)
+def test_chirp_time_energy_balance(q, c1, c2):
+    """The oracle's t(f) equals the chirp time derived by energy balance from the published E(x)
+    and F(x) (non-spinning through 3.5PN, spin-orbit at 1.5PN and 2.5PN), plus -2 sigma v^4 for the
+    2PN spin-spin terms, to 1e-12 relative over v = 0.05..1. Every post-Newtonian coefficient of
+    the phase, the 3PN logarithm and the beta, gamma, sigma spin terms enter this comparison
+    through numbers that appear nowhere in the oracle."""
+    mc = 20.0
+    taus = _energy_balance_taus(q, c1, c2)
+    sigma = _sigma_aligned(q, c1, c2)
+    for v in np.linspace(0.05, 1.0, 40):
+        t_or, mtot, eta = _oracle_chirp_time(mc, q, c1, c2, v)
+        lv = math.log(v)
+        ser = sum(float(taus[k](lv)) * v ** k for k in range(8)) - 2.0 * sigma * v ** 4
+        t_pub = -5.0 * mtot * TSUN / (256.0 * eta * v ** 8) * ser
+        assert abs(t_or / t_pub - 1.0) < 1e-12, (q, c1, c2, v, t_or, t_pub)
+
+
 def test_spin_orbit_beta_identity():
     """beta = sum_i (113/12 (m_i/M)^2 + 25/4 eta) chi_i (per-body form of the 1.5PN spin-orbit term)."""
     rng = np.random.default_rng(0)
@@ -211,11 +348,6 @@ def test_injection_snr_rescale():
     model = helpers.oracle_model(w)
     th = helpers.injection(w, 0)
     assert helpers.snr(w, model, th) == pytest.approx(20.0, rel=1e-9) or th[4] in (100.0, 5000.0)
-
-
-def _fd_ok(model, ev, th, widths, lnl_fn):
-    """Central differences with h = 1e-6 relative; skip components whose step moves the f_ISCO bin."""
-    return True
 
 
 def test_gradient_central_differences():
