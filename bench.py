@@ -56,8 +56,8 @@ WORK = {p: work(p) for p in ("mixed", "split", "fp64")}
 
 
 # DRAM bytes (read + write) of one NUTS launch of this workload from an ncu
-# capture (profiles/nuts_kernel_bbh11.md), valid only for the kernel sources
-# it was taken on: reported as roofline.traffic while their hash matches.
+# capture of the bench's own launch, valid only for the kernel sources it was
+# taken on: reported as roofline.traffic while their hash matches.
 TRAFFIC_SOURCES = ["nuts_kernel.cuh", "sweep.cuh", "physics.cuh", "common.cuh"]
 TRAFFIC = {"sources_sha256_16": "d0074ef565d4152d",
            "mixed": 3990016, "split": 3956480}
@@ -278,6 +278,66 @@ def main_loglike(args):
     return 0
 
 
+def _extra_workloads(args, flush):
+    """The other single-GPU workloads, measured after the timed region (CUDA events, L2 flushed before each
+    timed call): one bbh11_long SMC run per precision (16384 particles, covariance metric, after one untimed
+    run that also tunes the slot count), sharpy_loglike_grad on 8192 near-injection vectors of the 259585-bin
+    bns event (mixed and FP64), and one batched run of the 64-event batch64 workload (after one untimed run
+    that tunes it)."""
+    import torch
+
+    from paper_2601_02336_gb300 import api, inputs
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    out = {}
+    w = inputs.bbh11_long()
+    ctx, _, _ = api.make_event(w, seed=0)
+    ra = (w.n_particles, w.alpha, w.n_mut, w.max_depth, w.metric, w.eps_scale)
+    row = {"workload": _describe(w)}
+    for prec in ("mixed", "fp64"):
+        ctx.smc_run(*ra, key=40_000, precision=prec)
+        (lnz, _, _, rec), ms = timed(lambda: ctx.smc_run(*ra, key=40_001, precision=prec))
+        ev = sum(r["n_leapfrog"] for r in rec)
+        row[prec] = {"ms_per_run": ms, "evals_per_s": ev / (ms * 1e-3), "stages": len(rec), "lnz": lnz}
+    out["bbh11_long_smc_run"] = row
+    del ctx
+    w = inputs.bns()
+    ctx, th_inj, _ = api.make_event(w, seed=0)
+    th = torch.tensor(inputs.ball(w, th_inj, 8192, 2, rel=1e-3), dtype=torch.float64, device="cuda")
+    row = {"workload": "bns: 259585 bins x 3 detectors, 8192 vectors near the injection (sigma 1e-3 of the "
+                       "prior width), one sharpy_loglike_grad call = ln L + gradient of all 8192",
+           "active_bin_det_per_eval": float(_active_bins(w, th.cpu().numpy()).mean())}
+    for prec in ("mixed", "fp64"):
+        ctx.loglike_grad(th, prec)
+        _, ms = timed(lambda: ctx.loglike_grad(th, prec))
+        row[prec] = {"ms_per_call": ms, "evals_per_s": 8192 / (ms * 1e-3)}
+    out["bns_loglike_grad"] = row
+    del ctx, th
+    ws = inputs.batch64()
+    ctxs = [api.make_event(wi, seed=i)[0] for i, wi in enumerate(ws)]
+    w0 = ws[0]
+    b = api.Batch(ctxs, [wi.n_particles for wi in ws], w0.alpha, w0.n_mut, w0.max_depth, w0.metric, w0.eps_scale,
+                  precision="mixed", max_stages=500)
+    b.run([50_000 + e for e in range(len(ws))])
+    (res, rounds), ms = timed(lambda: b.run([60_000 + e for e in range(len(ws))]))
+    out["batch64_run"] = {"workload": "batch64: 64 events, segments 4/8/16/32 s, 512-8192 particles, depth 8, "
+                                      "mixed precision, one batched run of all 64 events",
+                          "ms_per_run": ms, "events_per_hour": len(ws) / (ms * 1e-3) * 3600.0,
+                          "evals_per_s": sum(r["n_leapfrog"] for r in res) / (ms * 1e-3), "rounds": rounds,
+                          "slots": b.slots}
+    b.close()
+    return out
+
+
 def main_batch(args):
     """64 uneven events (4/8/16/32 s segments, 512-8192 particles, NUTS depth 8)
     sampled together by the batched driver: one step = one batched run of all
@@ -367,7 +427,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sharpy", choices=["sharpy", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "split", "fp64"])
-    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=8,
+                    help="FP64 runs for the mixed-vs-FP64 comparison (ln Z within 2 combined standard errors)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the extra keys: the other single-GPU workloads, measured after the timed region")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="bbh11", choices=["tiny", "bbh11", "bbh11_long", "bns", "batch64"])
@@ -527,6 +590,10 @@ def main():
         e2e = {"value": allsum(e_evals) / e_max, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
+    extra = None
+    if rank == 0 and world == 1 and not args.no_extra and args.workload == "bbh11":
+        extra = _extra_workloads(args, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -553,7 +620,8 @@ def main():
                           "stages_per_run": n_stages},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk, "mixed_vs_fp64": other,
-               "lnz": {"mean": float(np.mean(lnzs)), "runs": [float(x) for x in lnzs]}}
+               "lnz": {"mean": float(np.mean(lnzs)), "runs": [float(x) for x in lnzs]},
+               "other_workloads": extra}
         print(json.dumps(out))
     if world > 1:
         dist.barrier()

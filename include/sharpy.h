@@ -138,6 +138,8 @@ typedef struct {
   double active_bins;  /* sum over the stage's gradient evaluations of (bins below f_ISCO) x detectors */
   double nuts_ms;      /* duration of the stage's NUTS launch (opt->timing = 1), else 0 */
   double reweight_ms;  /* duration of the stage's reweight/resample/gather (opt->timing = 1), else 0 */
+  double lnz;          /* ln Z after this stage: the running sum of the increments (Sec. 3.1, Eq. 8),
+                          accumulated on the device */
 } sharpy_stage;
 
 /* Context. Owns the staged data tables, scratch, the evidence accumulator and
@@ -191,6 +193,41 @@ int sharpy_nuts_mutate(sharpy_ctx* ctx, int64_t n, double beta, double* theta, d
                        uint64_t key, uint64_t ctr, int precision, sharpy_nuts_stats* stats,
                        sharpy_stream stream);
 
+/* sharpy_nuts_mutate with the identity metric and the step size of the
+   identity-metric runs (Sec. 6 gives step 0.5 for its Hessian metric; with
+   an identity mass matrix the step is scaled by the stage's particle spread):
+   step = eps_scale * min_j sqrt(cov[j][j]), computed on the device from the
+   weighted covariance cov [D][D] (device, e.g. the one
+   sharpy_smc_reweight_resample writes), so a host-side stage loop needs no
+   readback. SHARPY_EINVAL as sharpy_nuts_mutate, or if cov is NULL or
+   eps_scale is not positive and finite. */
+int sharpy_nuts_mutate_cov_step(sharpy_ctx* ctx, int64_t n, double beta, double* theta, double* lnl,
+                                double* grad, const double* cov, double eps_scale, int max_depth, int n_steps,
+                                uint64_t key, uint64_t ctr, int precision, sharpy_nuts_stats* stats,
+                                sharpy_stream stream);
+
+/* Failure detection: the persistent NUTS kernel bounds its tick loop (one
+   tick = one leapfrog of every slot with a pending evaluation) by
+   n_steps (2^max_depth + 1) + 4, which no valid trajectory reaches; on
+   reaching the bound it records SHARPY_ETIMEOUT in the status word and writes
+   back each particle's current proposal (a point of its trajectory with its
+   own ln L and gradient). max_ticks > 0 lowers that bound for the context's
+   later NUTS launches (single-event calls and sharpy_smc_run), so that tests
+   can drive the bound without a fault; 0 restores the default. SHARPY_EINVAL
+   for max_ticks < 0. */
+int sharpy_set_nuts_tick_limit(sharpy_ctx* ctx, int64_t max_ticks);
+
+/* Particle sharding of one event over several GPUs (one context per GPU,
+   Sec. 7 names splitting the particles across devices as the way to scale
+   out): the particle arrays given to this context's later prior draws and
+   NUTS calls (sharpy_prior_sample, sharpy_nuts_mutate*, and those inside
+   sharpy_smc_run) are rows first_id .. first_id + N - 1 of a larger ensemble.
+   Row i draws the random numbers of ensemble index first_id + i (the Philox
+   counter's particle word), so a shard computes exactly what a single call
+   over the whole ensemble computes for those rows. 0 (the default) is an
+   unsharded ensemble. SHARPY_EINVAL for first_id outside [0, 2^31). */
+int sharpy_set_shard(sharpy_ctx* ctx, int64_t first_id);
+
 /* sharpy_nuts_mutate with one metric per particle (the local metric of
    Sec. 5, e.g. from sharpy_local_metric): inv_mass [N][D][D] = M_i^-1 and
    chol [N][D][D] = L_i lower triangular with L_i L_i^T = M_i^-1 (device,
@@ -219,8 +256,10 @@ int sharpy_smc_reweight_resample(sharpy_ctx* ctx, int64_t n, double* theta, doub
    [0,1] (device), q_i = floor(W_i 2^32), C = inclusive prefix sum,
    U = floor(u 2^32), p_m = floor((m 2^32 + U) C_{N-1} / (N 2^32)),
    ancestor(m) = min{ j : C_j > p_m }. anc [N] int32 device. Needs no context.
-   SHARPY_EINVAL if u is outside [0,1) or N is outside [1, 1<<20]. An all-zero
-   W is reported through ancestors = -1. */
+   SHARPY_EINVAL if u is outside [0,1) or N is outside [1, 1<<20]; also if
+   some W_i is outside [0,1] or not finite, in which case the ancestors are
+   still written, with that weight taken as 0. An all-zero W is reported
+   through ancestors = -1. Synchronises `stream`. */
 int sharpy_systematic_resample(int64_t n, const double* w, double u, int32_t* anc, sharpy_stream stream);
 
 /* Allocation-free variant of sharpy_systematic_resample, with the same
@@ -232,10 +271,11 @@ int sharpy_systematic_resample(int64_t n, const double* w, double u, int32_t* an
    integer prefix sums and an invalid-weight flag) is a fixed device array
    inside the library, sized for N <= 262144 (2 MiB), which every GPU that
    loads the library keeps until the process exits. N above that returns
-   SHARPY_EINVAL; it allocates nothing (no cudaMalloc/cudaFree, no allocating
-   library call). The first call on a device, with that device current, looks
-   up the array's device address; make that first call before any stream
-   capture. All calls share the one array, which keeps the last call's
+   SHARPY_EINVAL, as does a weight outside [0,1] (ancestors still written, that
+   weight taken as 0); it allocates nothing (no cudaMalloc/cudaFree, no
+   allocating library call). Every call looks up the array's device address on
+   the current device (a lookup, not an allocation). All calls share the one
+   array, which keeps the last call's
    contents (the flag is cleared by each call): calls that overlap on the GPU
    (other streams, other threads) race and must be serialised by the caller.
    Synchronises `stream` (like sharpy_systematic_resample). */
@@ -244,6 +284,10 @@ int sharpy_systematic_resample_static(int64_t n, const double* w, double u, int3
 
 /* Reset the context's evidence accumulator (ln Z = 0, zero stages). */
 int sharpy_reset_evidence(sharpy_ctx* ctx, sharpy_stream stream);
+/* Set the context's evidence accumulator to ln Z = lnz after n_stages stages
+   (resuming a run from a stage-boundary checkpoint). Synchronises `stream`.
+   SHARPY_EINVAL for a non-finite lnz or n_stages < 0. */
+int sharpy_set_evidence(sharpy_ctx* ctx, double lnz, int n_stages, sharpy_stream stream);
 /* Sum of the evidence increments since the last reset (Sec. 3.1, Eq. 8) and
    the number of stages. Synchronises the context's last stream. */
 int sharpy_log_evidence(sharpy_ctx* ctx, double* lnz, int* n_stages);
@@ -270,7 +314,8 @@ int sharpy_smc_run(sharpy_ctx* ctx, const sharpy_smc_options* opt, uint64_t key,
    same model kind and detector count; n_particles[e]: particles of event e
    (HOST array); opt: alpha, n_mut, max_depth, metric, eps_scale, precision,
    max_stages as in sharpy_smc_run (opt->n_particles and opt->timing are
-   ignored). The contexts must outlive the batch. Allocates the batch's device
+   ignored). The contexts must outlive the batch and be unsharded
+   (sharpy_set_shard 0). Allocates the batch's device
    memory (particles of all events, stage scratch, records). Synchronous. */
 typedef struct sharpy_batch sharpy_batch;
 typedef struct {

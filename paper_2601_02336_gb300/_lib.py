@@ -51,7 +51,7 @@ class Stage(C.Structure):
                 ("dlnz", C.c_double), ("eps", C.c_double), ("accept_mean", C.c_double),
                 ("depth_mean", C.c_double), ("n_leapfrog", C.c_int64), ("n_divergent", C.c_int),
                 ("pad", C.c_int), ("active_bins", C.c_double), ("nuts_ms", C.c_double),
-                ("reweight_ms", C.c_double)]
+                ("reweight_ms", C.c_double), ("lnz", C.c_double)]
 
 
 class BatchResult(C.Structure):
@@ -78,6 +78,7 @@ _SIGS = {
     "sharpy_systematic_resample": (C.c_int, [C.c_int64, _VP, C.c_double, _VP, _VP]),
     "sharpy_systematic_resample_static": (C.c_int, [C.c_int64, _VP, C.c_double, _VP, _VP]),
     "sharpy_reset_evidence": (C.c_int, [_CTX, _VP]),
+    "sharpy_set_evidence": (C.c_int, [_CTX, C.c_double, C.c_int, _VP]),
     "sharpy_log_evidence": (C.c_int, [_CTX, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "sharpy_smc_run": (C.c_int, [_CTX, C.POINTER(SmcOptions), C.c_uint64, C.POINTER(C.c_double),
                                  C.POINTER(C.c_int), _VP, _VP, C.POINTER(Stage), _VP]),
@@ -91,6 +92,10 @@ _SIGS = {
     "sharpy_batch_slots": (C.c_int, [_VP]),
     "sharpy_batch_set_slots": (C.c_int, [_VP, C.c_int]),
     "sharpy_batch_launches": (C.c_int64, [_VP]),
+    "sharpy_nuts_mutate_cov_step": (C.c_int, [_CTX, C.c_int64, C.c_double, _VP, _VP, _VP, _VP, C.c_double,
+                                              C.c_int, C.c_int, C.c_uint64, C.c_uint64, C.c_int, _VP, _VP]),
+    "sharpy_set_nuts_tick_limit": (C.c_int, [_CTX, C.c_int64]),
+    "sharpy_set_shard": (C.c_int, [_CTX, C.c_int64]),
     "sharpy_nuts_mutate_local": (C.c_int, [_CTX, C.c_int64, C.c_double, _VP, _VP, _VP, _VP, _VP, C.c_double,
                                            C.c_int, C.c_int, C.c_uint64, C.c_uint64, C.c_int, _VP, _VP]),
     "sharpy_local_metric": (C.c_int, [_CTX, C.c_int64, _VP, C.c_double, _VP, _VP, _VP, _VP]),

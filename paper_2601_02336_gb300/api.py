@@ -167,6 +167,26 @@ class Context:
                                              _prec(precision), _ptr(st), _stream()), "sharpy_nuts_mutate_local")
         return st
 
+    def nuts_mutate_cov_step(self, beta, theta, lnl, grad, cov, eps_scale, max_depth, n_steps, key, ctr,
+                             precision="mixed", stats=True):
+        """nuts_mutate with the identity metric and step = eps_scale * min_j sqrt(cov[j][j]), the step
+        taken on the device from the weighted covariance cov [D][D] (device)."""
+        n = theta.shape[0]
+        st = torch.empty(n * STATS_DTYPE.itemsize, dtype=torch.uint8, device=theta.device) if stats else None
+        check(lib().sharpy_nuts_mutate_cov_step(self._h, n, beta, _ptr(_dev(theta, "theta")), _ptr(_dev(lnl, "lnl")),
+                                                _ptr(_dev(grad, "grad")), _ptr(_dev(cov, "cov")), eps_scale,
+                                                max_depth, n_steps, key, ctr, _prec(precision), _ptr(st),
+                                                _stream()), "sharpy_nuts_mutate_cov_step")
+        return st
+
+    def set_shard(self, first_id):
+        """Later prior draws and NUTS calls act on rows first_id.. of a larger ensemble (sharpy_set_shard)."""
+        check(lib().sharpy_set_shard(self._h, int(first_id)), "sharpy_set_shard")
+
+    def set_nuts_tick_limit(self, max_ticks):
+        """Lower the NUTS kernel's tick bound (failure-detection tests); 0 restores the default."""
+        check(lib().sharpy_set_nuts_tick_limit(self._h, int(max_ticks)), "sharpy_set_nuts_tick_limit")
+
     @staticmethod
     def stats_to_numpy(st):
         return np.frombuffer(st.cpu().numpy().tobytes(), dtype=STATS_DTYPE)
@@ -185,6 +205,9 @@ class Context:
 
     def reset_evidence(self):
         check(lib().sharpy_reset_evidence(self._h, _stream()), "sharpy_reset_evidence")
+
+    def set_evidence(self, lnz, n_stages):
+        check(lib().sharpy_set_evidence(self._h, float(lnz), int(n_stages), _stream()), "sharpy_set_evidence")
 
     def log_evidence(self):
         lnz = C.c_double()
@@ -267,6 +290,7 @@ class SMCRunner:
         o = self.opts
         self.theta = self.ctx.prior_sample(o["n_particles"], o["key"], 0)
         self.lnl, self.grad = self.ctx.loglike_grad(self.theta, o["precision"])
+        self.ctx.reset_evidence()
         self.beta, self.lnz, self.stage, self.records = 0.0, 0.0, 0, []
         return self
 
@@ -291,14 +315,15 @@ class SMCRunner:
             st = self.ctx.nuts_mutate(beta_next, self.theta, self.lnl, self.grad, r["cov"], o["eps_scale"], *args,
                                       precision=o["precision"])
         else:
-            eps = o["eps_scale"] * float(np.sqrt(np.diag(r["cov"].cpu().numpy())).min())
-            st = self.ctx.nuts_mutate(beta_next, self.theta, self.lnl, self.grad, None, eps, *args,
-                                      precision=o["precision"])
+            st = self.ctx.nuts_mutate_cov_step(beta_next, self.theta, self.lnl, self.grad, r["cov"], o["eps_scale"],
+                                               *args, precision=o["precision"])
         s = Context.stats_to_numpy(st)
+        # ln Z: the context's device accumulator of the stage increments (Eq. 8)
+        lnz, _ = self.ctx.log_evidence()
         self.records.append({"beta": beta_next, "dlnz": dlnz, "ess": float(r["ess"]),
-                             "n_leapfrog": int(s["n_leapfrog"].sum())})
+                             "n_leapfrog": int(s["n_leapfrog"].sum()), "lnz": lnz})
         self.beta = beta_next
-        self.lnz += dlnz
+        self.lnz = lnz
         return self
 
     def run(self):
@@ -325,6 +350,7 @@ class SMCRunner:
         r.grad = torch.tensor(z["grad"], dtype=torch.float64, device=dev)
         beta, lnz, stage = (float(x) for x in z["scalars"])
         r.beta, r.lnz, r.stage = beta, lnz, int(stage)
+        ctx.set_evidence(lnz, int(stage))
         r.records = ast.literal_eval(str(z["records"]))
         return r
 
@@ -419,10 +445,11 @@ def recycle(theta, lnl, betas, lnz_t, key):
 
 
 def recycle_run(pool_theta, pool_lnl, records, n_particles, key):
-    """Recycle the pool of an smc_run(..., pool_stages=T): its stages' beta and running ln Z."""
+    """Recycle the pool of an smc_run(..., pool_stages=T): its stages' beta and running ln Z (the stage
+    records' device-accumulated ln Z)."""
     t = pool_theta.shape[0] // n_particles
     betas = [r["beta"] for r in records[:t]]
-    lnz_t = np.cumsum([r["dlnz"] for r in records[:t]])
+    lnz_t = [r["lnz"] for r in records[:t]]
     return recycle(pool_theta, pool_lnl, betas, lnz_t, key)
 
 

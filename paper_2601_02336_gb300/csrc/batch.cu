@@ -29,7 +29,7 @@ int ensure_fisher_tables(sharpy_ctx* c);
 int enqueue_local_metric(sharpy_ctx* c, int64_t n, const double* theta, const double* beta_ptr, double beta,
                          double* mass, double* minv, double* chol, cudaStream_t s);
 
-constexpr int kBatchRec = 9;  // beta, ess, dlnz, eps, accept, depth, leapfrogs, divergent, active bins
+constexpr int kBatchRec = 10;  // beta, ess, dlnz, eps, accept, depth, leapfrogs, divergent, active bins, ln Z
 constexpr int kRoundsPerCheck = 4;
 constexpr int kTuneRound = 3;  // the first run tunes the slot count on this round (full mutations on copies)
 
@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(256) batch_record_kernel(const StageArgs* sa, 
       eps = eps_scale * smin;
     }
     r[3] = eps;
+    r[9] = A.lnz_acc[0];
     tot[2 * e] += r[6];
     tot[2 * e + 1] += r[8];
     done[e] = (*A.beta_next >= 1.0 || t >= max_stages) ? 1 : 0;
@@ -238,7 +239,8 @@ int sharpy_batch_create(sharpy_batch** out, sharpy_ctx* const* events, int n_eve
     sharpy_ctx* c = events[e];
     const int64_t ne = n_particles[e];
     int rc = check_ctx(c, true);
-    if (rc || c->device != events[0]->device || c->model.model != kind || ne < 1 || ne > kMaxParticles) {
+    if (rc || c->device != events[0]->device || c->model.model != kind || ne < 1 || ne > kMaxParticles ||
+        c->first_id != 0) {
       delete b;
       return rc ? rc : SHARPY_EINVAL;
     }
@@ -566,6 +568,7 @@ int sharpy_batch_stages(sharpy_batch* b, int e, sharpy_stage* stages, int cap, i
     g.active_bins = q[8];
     g.nuts_ms = 0.0;
     g.reweight_ms = 0.0;
+    g.lnz = q[9];
   }
   *n = m;
   return SHARPY_OK;

@@ -286,6 +286,21 @@ int sharpy_reset_evidence(sharpy_ctx* c, sharpy_stream stream) {
   return SHARPY_OK;
 }
 
+int sharpy_set_evidence(sharpy_ctx* c, double lnz, int n_stages, sharpy_stream stream) {
+  int rc = check_ctx(c, false);
+  if (rc) return rc;
+  if (!std::isfinite(lnz) || n_stages < 0) return SHARPY_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  // through the pinned staging buffer, after the stream's earlier work has read it
+  SHARPY_CUDA_TRY(cudaStreamSynchronize(s));
+  c->h_pinned[0] = lnz;
+  c->h_pinned[1] = (double)n_stages;
+  SHARPY_CUDA_TRY(cudaMemcpyAsync(c->d_lnz, c->h_pinned, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+  SHARPY_CUDA_TRY(cudaStreamSynchronize(s));
+  c->last_stream = s;
+  return SHARPY_OK;
+}
+
 int sharpy_log_evidence(sharpy_ctx* c, double* lnz, int* n_stages) {
   int rc = check_ctx(c, false);
   if (rc) return rc;

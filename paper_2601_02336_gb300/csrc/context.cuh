@@ -36,6 +36,8 @@ struct sharpy_ctx {
   double* d_p2 = nullptr;       // [n_det][kNBasis (kNBasis + 1) / 2][K] prefix sums of w f^-7/3 B_m B_n
   // NUTS slot count picked by the autotuner, per precision and metric kind
   // (shared / per-particle), for tuned_n[p][l] particles (0: not tuned)
+  int64_t nuts_tick_limit = 0;
+  int64_t first_id = 0;         // ensemble index of row 0 of the particle arrays (sharpy_set_shard)  // > 0: lowered NUTS tick bound (sharpy_set_nuts_tick_limit)
   int tuned_slots[3][2] = {};
   int64_t tuned_n[3][2] = {{-1, -1}, {-1, -1}, {-1, -1}};
 };

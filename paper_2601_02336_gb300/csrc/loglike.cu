@@ -116,12 +116,13 @@ __global__ void waveform_kernel(DevModel m, DevEvent ev, int64_t n, const double
   }
 }
 
-__global__ void prior_sample_kernel(DevModel m, int64_t n, double* __restrict__ theta, uint64_t key, uint32_t ctr) {
+__global__ void prior_sample_kernel(DevModel m, int64_t n, double* __restrict__ theta, uint64_t key, uint32_t ctr,
+                                    int64_t first) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   for (int i = 0; i < m.n_dim; ++i) {
     double u0, u1;
-    uniform2(key, (uint32_t)p, ctr, RNG_PRIOR, (uint32_t)i, &u0, &u1);
+    uniform2(key, (uint32_t)(p + first), ctr, RNG_PRIOR, (uint32_t)i, &u0, &u1);
     double lo = m.lo[i], hi = m.hi[i], x;
     if (m.prior[i] == SHARPY_PRIOR_POWER2)
       x = cbrt(lo * lo * lo + u0 * (hi * hi * hi - lo * lo * lo));
@@ -203,7 +204,8 @@ int sharpy_prior_sample(sharpy_ctx* c, int64_t n, double* theta, uint64_t key, u
   if (n == 0) return SHARPY_OK;
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
-  prior_sample_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(c->model, n, theta, key, (uint32_t)ctr);
+  prior_sample_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(c->model, n, theta, key, (uint32_t)ctr,
+                                                                   c->first_id);
   return cudaGetLastError() == cudaSuccess ? SHARPY_OK : SHARPY_ECUDA;
 }
 

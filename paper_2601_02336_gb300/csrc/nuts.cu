@@ -56,6 +56,8 @@ int enqueue_nuts(sharpy_ctx* c, int64_t n, const double* beta_ptr, double beta, 
   A.ctr = ctr;
   A.stats = stats;
   A.status = c->d_status;
+  A.tick_limit = c->nuts_tick_limit;
+  A.id_offset = c->first_id;
   const int lm = pminv ? 1 : 0;
   if (!slots && c->tuned_slots[precision][lm] && c->tuned_n[precision][lm] == n) slots = c->tuned_slots[precision][lm];
   if (!slots) {
@@ -111,4 +113,39 @@ extern "C" int sharpy_nuts_mutate_local(sharpy_ctx* c, int64_t n, double beta, d
   c->last_stream = s;
   return enqueue_nuts(c, n, nullptr, beta, theta, lnl, grad, nullptr, nullptr, step, max_depth, n_steps, key,
                       (uint32_t)ctr, precision, stats, s, 0, inv_mass, chol);
+}
+
+extern "C" int sharpy_nuts_mutate_cov_step(sharpy_ctx* c, int64_t n, double beta, double* theta, double* lnl,
+                                           double* grad, const double* cov, double eps_scale, int max_depth,
+                                           int n_steps, uint64_t key, uint64_t ctr, int precision,
+                                           sharpy_nuts_stats* stats, sharpy_stream stream) {
+  int rc = check_ctx(c, true);
+  if (rc) return rc;
+  if (n < 0 || n > ((int64_t)1 << 31) - 1) return SHARPY_EINVAL;
+  if (n == 0) return SHARPY_OK;
+  if (!theta || !lnl || !grad || !cov || !(eps_scale > 0.0) || !isfinite(eps_scale) || max_depth < 0 ||
+      max_depth > kMaxDepth || n_steps < 0 || !(beta >= 0.0 && beta <= 1.0))
+    return SHARPY_EINVAL;
+  if (precision != SHARPY_FP64 && precision != SHARPY_MIXED && precision != SHARPY_MIXED_SPLIT)
+    return SHARPY_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  return enqueue_nuts(c, n, nullptr, beta, theta, lnl, grad, nullptr, cov, eps_scale, max_depth, n_steps, key,
+                      (uint32_t)ctr, precision, stats, s, 0, nullptr, nullptr);
+}
+
+extern "C" int sharpy_set_nuts_tick_limit(sharpy_ctx* c, int64_t max_ticks) {
+  int rc = check_ctx(c, false);
+  if (rc) return rc;
+  if (max_ticks < 0) return SHARPY_EINVAL;
+  c->nuts_tick_limit = max_ticks;
+  return SHARPY_OK;
+}
+
+extern "C" int sharpy_set_shard(sharpy_ctx* c, int64_t first_id) {
+  int rc = check_ctx(c, false);
+  if (rc) return rc;
+  if (first_id < 0 || first_id > ((int64_t)1 << 31) - 1) return SHARPY_EINVAL;
+  c->first_id = first_id;
+  return SHARPY_OK;
 }

@@ -84,6 +84,8 @@ struct NutsArgs {
   uint32_t ctr;
   sharpy_nuts_stats* stats;
   int* status;
+  int64_t tick_limit;      // > 0: lowered tick bound (failure-detection tests); 0: the default
+  int64_t id_offset;       // ensemble index of row 0: names the rows' random numbers (a shard of an ensemble)
   // batched driver (null otherwise): CTA b runs block cta_map[b].y of event
   // cta_map[b].x, whose arguments are batch[cta_map[b].x]; an event's CTAs
   // return at once while *active == 0, and its counter is *stage << 8
@@ -368,7 +370,7 @@ struct Nuts {
 
   __device__ void draw_direction(Slot<VT>& sl) {
     VT u0, u1;
-    draw2(A.key, (uint32_t)sl.pid, A.ctr + (uint32_t)sl.t, RNG_DIRECTION, (uint32_t)sl.depth, &u0, &u1);
+    draw2(A.key, (uint32_t)(sl.pid + A.id_offset), A.ctr + (uint32_t)sl.t, RNG_DIRECTION, (uint32_t)sl.depth, &u0, &u1);
     sl.dir = u0 < VT(0.5) ? -1 : 1;
     sl.n = 0;
     sl.logw_sub = -INFINITY;
@@ -386,7 +388,7 @@ struct Nuts {
       const int d = dim(k);
       if (!has(k)) continue;
       VT u0, u1;
-      draw2(A.key, (uint32_t)sl.pid, step, RNG_MOMENTUM, (uint32_t)(d >> 1), &u0, &u1);
+      draw2(A.key, (uint32_t)(sl.pid + A.id_offset), step, RNG_MOMENTUM, (uint32_t)(d >> 1), &u0, &u1);
       const VT r = vsqrt(VT(-2) * vlog(u0));
       VT sn, cs;
       vsincospi(VT(2) * u1, &sn, &cs);
@@ -496,7 +498,7 @@ struct Nuts {
         const VT lw = -dH;
         const VT lw_new = logaddexp(sl.logw_sub, lw);
         VT u0, u1;
-        draw2(A.key, (uint32_t)sl.pid, A.ctr + (uint32_t)sl.t, RNG_LEAF, sl.leaf_ctr++, &u0, &u1);
+        draw2(A.key, (uint32_t)(sl.pid + A.id_offset), A.ctr + (uint32_t)sl.t, RNG_LEAF, sl.leaf_ctr++, &u0, &u1);
         if (u0 < vexp(lw - lw_new)) {
 #pragma unroll
           for (int k = 0; k < DPL; ++k) {
@@ -539,7 +541,7 @@ struct Nuts {
           goto next_transition;
         }
         // sub-tree complete: biased progressive sampling at the top level
-        draw2(A.key, (uint32_t)sl.pid, A.ctr + (uint32_t)sl.t, RNG_TOP, (uint32_t)sl.depth, &u0, &u1);
+        draw2(A.key, (uint32_t)(sl.pid + A.id_offset), A.ctr + (uint32_t)sl.t, RNG_TOP, (uint32_t)sl.depth, &u0, &u1);
         if (u0 < vexp(sl.logw_sub - sl.logw)) {
 #pragma unroll
           for (int k = 0; k < DPL; ++k) {
@@ -760,7 +762,7 @@ __global__ void __launch_bounds__(kNutsWarps * 32, PREC == SHARPY_FP64 ? 2 : 3)
     }
   }
   __syncthreads();
-  const long max_ticks = (long)A.n_steps * ((1L << A.max_depth) + 1) + 4;
+  const long max_ticks = A.tick_limit > 0 ? (long)A.tick_limit : (long)A.n_steps * ((1L << A.max_depth) + 1) + 4;
   for (long tick = 0;; ++tick) {
     // warp 0: any pending evaluation left?
     if (warp == cw) {

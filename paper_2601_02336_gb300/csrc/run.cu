@@ -20,15 +20,15 @@ int enqueue_nuts(sharpy_ctx* c, int64_t n, const double* beta_ptr, double beta, 
 int enqueue_local_metric(sharpy_ctx* c, int64_t n, const double* theta, const double* beta_ptr, double beta,
                          double* mass, double* minv, double* chol, cudaStream_t s);
 
-// Per-stage record: [beta, ess, dlnz, eps, accept_sum, depth_sum, n_leapfrog, n_divergent, active_bins]
-constexpr int kRec = 9;
+// Per-stage record: [beta, ess, dlnz, eps, accept_sum, depth_sum, n_leapfrog, n_divergent, active_bins, ln Z]
+constexpr int kRec = 10;
 // Stage on which a context without a tuned slot count times the candidates
 // (a mid-run state; on the first stage every tree reaches the depth limit).
 constexpr int kTuneStage = 3;
 
 __global__ void stage_record_kernel(int64_t n, int D, const sharpy_nuts_stats* __restrict__ st,
                                     const double* beta, const double* ess, const double* dlnz, const double* cov,
-                                    int metric, double eps_scale, double* rec) {
+                                    int metric, double eps_scale, const double* lnz_acc, double* rec) {
   __shared__ double red[5][32];
   double a[5] = {0, 0, 0, 0, 0};
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
@@ -60,6 +60,7 @@ __global__ void stage_record_kernel(int64_t n, int D, const sharpy_nuts_stats* _
       eps = eps_scale * smin;
     }
     rec[3] = eps;
+    rec[9] = lnz_acc[0];
   }
 }
 }  // namespace sharpy
@@ -167,7 +168,8 @@ extern "C" int sharpy_smc_run(sharpy_ctx* c, const sharpy_smc_options* o, uint64
           cudaMemcpyAsync(o->pool_lnl + row, ll, n * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return fail(SHARPY_ECUDA);
     }
-    stage_record_kernel<<<1, 1024, 0, s>>>(n, D, st, beta_next, ess, dlnz, cov, o->metric, o->eps_scale, rec);
+    stage_record_kernel<<<1, 1024, 0, s>>>(n, D, st, beta_next, ess, dlnz, cov, o->metric, o->eps_scale, c->d_lnz,
+                                           rec);
     if (cudaGetLastError() != cudaSuccess) return fail(SHARPY_ECUDA);
     if (cudaMemcpyAsync(c->h_pinned, rec, kRec * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
@@ -193,6 +195,7 @@ extern "C" int sharpy_smc_run(sharpy_ctx* c, const sharpy_smc_options* o, uint64
       }
       g.nuts_ms = ms;
       g.reweight_ms = rms;
+      g.lnz = r[9];
     }
     beta = r[0];
     if (!std::isfinite(beta)) return fail(SHARPY_ENONFINITE);

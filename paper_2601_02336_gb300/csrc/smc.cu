@@ -580,7 +580,10 @@ int sharpy_systematic_resample(int64_t n, const double* w, double u, int32_t* an
   int* bad = nullptr;
   if (cudaMallocAsync((void**)&C, n * sizeof(unsigned long long) + 16, s) != cudaSuccess) return SHARPY_ENOMEM;
   bad = (int*)(C + n);
-  SHARPY_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  if (cudaMemsetAsync(bad, 0, sizeof(int), s) != cudaSuccess) {
+    cudaFreeAsync(C, s);
+    return SHARPY_ECUDA;
+  }
   prefix_kernel<<<1, kSmcThreads, 0, s>>>(n, w, C, bad);
   unsigned long long U = (unsigned long long)floor(u * 4294967296.0);
   systematic_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, C, U, anc);
@@ -600,35 +603,22 @@ int sharpy_systematic_resample(int64_t n, const double* w, double u, int32_t* an
 // they are running. Its scratch (the prefix sums and an invalid-weight flag)
 // is a file-scope device array of fixed size; every device that loads the
 // library keeps it until the process exits.
-#include <mutex>
-
 namespace sharpy {
 constexpr int64_t kStaticResampleMax = (int64_t)1 << 18;  // 262144 particles (2 MiB of scratch)
 static __device__ __align__(256) unsigned long long g_resample_scratch[kStaticResampleMax + 32];
-constexpr int kStaticMaxDevices = 64;
-static unsigned long long* g_resample_scratch_addr[kStaticMaxDevices];
-static std::mutex g_resample_scratch_mu;
 }  // namespace sharpy
 
 extern "C" int sharpy_systematic_resample_static(int64_t n, const double* w, double u, int32_t* anc,
                                                  sharpy_stream stream) {
   using namespace sharpy;
   if (n < 1 || n > kStaticResampleMax || !w || !anc || !(u >= 0.0 && u < 1.0)) return SHARPY_EINVAL;
-  int dev = 0;
-  SHARPY_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kStaticMaxDevices) return SHARPY_EINVAL;
-  unsigned long long* base = nullptr;
-  {
-    // One-time set-up per device (the current one): the host-side name of the
-    // array is only a stand-in, so fetch its device address.
-    std::lock_guard<std::mutex> lock(g_resample_scratch_mu);
-    if (!g_resample_scratch_addr[dev]) {
-      void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_resample_scratch) != cudaSuccess || !p) return SHARPY_ECUDA;
-      g_resample_scratch_addr[dev] = (unsigned long long*)p;
-    }
-    base = g_resample_scratch_addr[dev];
-  }
+  // The host-side name of the array is only a stand-in: fetch its device
+  // address on the current device, on every call (a lookup, no allocation),
+  // so that the address stays right after a device reset or in another
+  // context.
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_resample_scratch) != cudaSuccess || !p) return SHARPY_ECUDA;
+  unsigned long long* base = (unsigned long long*)p;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned long long* C = base;
   int* bad = (int*)(base + kStaticResampleMax);

@@ -95,3 +95,31 @@ def test_batch_rejects_mixed_detector_counts():
     c = api.make_event(w, seed=0)[0]
     with pytest.raises(SharpyError):
         api.Batch([a, c], [64, 64], 0.5, 2, 4, 0, 0.5)
+
+
+def test_batch_event_lnz_vs_oracle_runs():
+    """One event of the batched recipe (4 s segment, 4017 bins, 256 particles, depth 8) run inside a
+    two-event batch: ln Z over R = 8 keys against the oracle's full SMC runs of that event
+    (tests/golden, written by tests/golden/make_lnz_oracle.py from the oracle alone), within two
+    combined standard errors."""
+    import json
+    import math
+    import os
+
+    import numpy as np
+    G.require_gpu()
+    with open(os.path.join(os.path.dirname(__file__), "golden", "lnz_batch1_oracle.json")) as fh:
+        gold = json.load(fh)
+    ws = inputs.batch64()
+    w, w2 = ws[5], ws[16]
+    w.n_particles, w2.n_particles = gold["n_particles"], 192
+    assert gold["n_bins"] == w.n_bins and gold["max_depth"] == w.max_depth
+    _, ctx, _, _ = G.event_pair(w, seed=gold["event_seed"])
+    ctx2 = api.make_event(w2, seed=16)[0]
+    b = api.Batch([ctx, ctx2], [w.n_particles, w2.n_particles], alpha=w.alpha, n_mut=w.n_mut,
+                  max_depth=w.max_depth, metric=w.metric, eps_scale=w.eps_scale, precision="mixed", max_stages=200)
+    got = [b.run([7300 + s, 7400 + s])[0][0]["lnz"] for s in range(8)]
+    ref = [r["lnz"] for r in gold["runs"]]
+    assert len(ref) >= 6
+    se = lambda x: np.std(x, ddof=1) / math.sqrt(len(x))
+    assert abs(np.mean(got) - np.mean(ref)) <= 2.0 * math.sqrt(se(got) ** 2 + se(ref) ** 2), (got, ref)

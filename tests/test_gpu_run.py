@@ -143,3 +143,29 @@ def test_run_local_metric_vs_oracle():
         ref.append(r[0])
         got.append(g[0])
     assert abs(np.mean(got) - np.mean(ref)) <= 2.0 * math.sqrt(_se(got) ** 2 + _se(ref) ** 2), (got, ref)
+
+
+def _golden(name):
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", f"lnz_{name}_oracle.json")
+    with open(path) as fh:
+        return json.load(fh)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_run_bbh11_lnz_vs_oracle_runs(precision):
+    """The 11-D, three-detector workload (8033 bins, 2048 particles, depth 6, identity metric): ln Z of
+    R = 8 GPU runs against the oracle's full SMC runs on the same event (tests/golden, written by
+    tests/golden/make_lnz_oracle.py from the oracle alone), within two combined standard errors."""
+    G.require_gpu()
+    gold = _golden("bbh11")
+    w = inputs.bbh11()
+    assert gold["n_particles"] == w.n_particles and gold["n_bins"] == w.n_bins
+    ev, ctx, th_inj, _ = G.event_pair(w, seed=gold["event_seed"])
+    ref = [r["lnz"] for r in gold["runs"]]
+    got = [ctx.smc_run(w.n_particles, w.alpha, w.n_mut, w.max_depth, w.metric, w.eps_scale, key=7100 + s,
+                       precision=precision)[0] for s in range(8)]
+    assert len(ref) >= 8
+    assert abs(np.mean(got) - np.mean(ref)) <= 2.0 * math.sqrt(_se(got) ** 2 + _se(ref) ** 2), (got, ref)
+    assert ctx.status() == 0

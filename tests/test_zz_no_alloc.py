@@ -60,3 +60,22 @@ def test_static_resample_limits_and_flag_reset():
     rc, got = _call(lib.sharpy_systematic_resample_static, good, 0.5)
     rc_ref, ref = _call(lib.sharpy_systematic_resample, good, 0.5)
     assert rc == 0 and rc_ref == 0 and torch.equal(got, ref)
+
+
+def test_static_resample_leaves_free_memory_unchanged():
+    """The point of the entry point: once running it takes no device memory. After a warm-up call
+    (which loads the kernels), 100 more calls leave the device's free memory as it was."""
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test run without a visible CUDA device")
+    lib = _lib.lib()
+    rng = np.random.default_rng(7)
+    wd = torch.tensor(rng.uniform(0, 1, 150_001), dtype=torch.float64, device="cuda")
+    rc, ref = _call(lib.sharpy_systematic_resample_static, wd, 0.25)
+    assert rc == 0
+    free0, _ = torch.cuda.mem_get_info()
+    for i in range(100):
+        rc, got = _call(lib.sharpy_systematic_resample_static, wd, 0.25)
+        assert rc == 0
+    free1, _ = torch.cuda.mem_get_info()
+    assert torch.equal(got, ref)
+    assert free1 == free0, (free0, free1)
