@@ -338,6 +338,51 @@ def _extra_workloads(args, flush):
     return out
 
 
+def main_nuts_launch(args):
+    """One persistent NUTS launch on fixed ensembles of the bbh11 event (2048 particles, depth 6, two
+    transitions, identity metric, step 0.5 x the ensemble's smallest standard deviation): "first" = prior
+    draws at beta = 1e-4 (the first stage's regime: most trees reach the depth limit), "late" = a Gaussian
+    ball around the injection (sigma 1e-3 of the prior width) at beta = 1 (a posterior-like stage). The
+    launches are deterministic, so versions of the kernel are compared on identical work; also the command
+    the instruction-count and DRAM captures of the roofline are taken on (--ensemble picks one)."""
+    import torch
+
+    from paper_2601_02336_gb300 import api, inputs
+    torch.cuda.set_device(0)
+    w = inputs.bbh11()
+    ctx, th_inj, _ = api.make_event(w, seed=0)
+    sets = {"first": (inputs.prior_draws(w, w.n_particles, 1), 1e-4),
+            "late": (inputs.ball(w, th_inj, w.n_particles, 2, rel=1e-3), 1.0)}
+    names = [args.ensemble] if args.ensemble else list(sets)
+    stream = torch.cuda.current_stream()
+    out = {"mode": "nuts_launch", "workload": _describe(w), "precision": args.precision, "ensembles": {}}
+    for name in names:
+        th, beta = sets[name]
+        eps = 0.5 * float(np.min(np.std(th, axis=0)))
+        t0 = torch.tensor(th, dtype=torch.float64, device="cuda")
+        l0, g0 = ctx.loglike_grad(t0, "fp64")
+        times, st = [], None
+        for k in range(args.warmup + args.steps):
+            t, l, g = t0.clone(), l0.clone(), g0.clone()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s = ctx.nuts_mutate(beta, t, l, g, None, eps, w.max_depth, w.n_mut, key=77, ctr=256,
+                                precision=args.precision)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+                st = api.Context.stats_to_numpy(s)
+        out["ensembles"][name] = {"beta": beta, "step": eps, "ms_median": float(np.median(times)),
+                                  "ms_min": float(np.min(times)), "launches": len(times),
+                                  "active_bin_det": float(st["active_bins"].sum()),
+                                  "n_leapfrog": int(st["n_leapfrog"].sum()),
+                                  "accept_mean": float(st["accept_sum"].mean() / w.n_mut)}
+    out["status"] = ctx.status()
+    print(json.dumps(out))
+    return 0
+
+
 def main_batch(args):
     """64 uneven events (4/8/16/32 s segments, 512-8192 particles, NUTS depth 8)
     sampled together by the batched driver: one step = one batched run of all
@@ -427,14 +472,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sharpy", choices=["sharpy", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "split", "fp64"])
-    ap.add_argument("--fp64-steps", type=int, default=8,
+    ap.add_argument("--fp64-steps", type=int, default=16,
                     help="FP64 runs for the mixed-vs-FP64 comparison (ln Z within 2 combined standard errors)")
+    ap.add_argument("--lnz-runs", type=int, default=16,
+                    help="mixed runs for that comparison: the timed runs plus untimed ones up to this count")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the extra keys: the other single-GPU workloads, measured after the timed region")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="bbh11", choices=["tiny", "bbh11", "bbh11_long", "bns", "batch64"])
-    ap.add_argument("--mode", default="smc", choices=["smc", "loglike"])
+    ap.add_argument("--mode", default="smc", choices=["smc", "loglike", "nuts_launch"])
+    ap.add_argument("--ensemble", default=None, choices=["first", "late"], help="nuts_launch: one ensemble only")
     ap.add_argument("--slots", type=int, default=0, choices=[0, 8, 16, 32],
                     help="batch64: NUTS particles per CTA (0: autotuned)")
     ap.add_argument("--metric", type=int, default=None, choices=[0, 1, 2],
@@ -444,6 +492,8 @@ def main():
         return run_reference(args)
     if args.mode == "loglike":
         return main_loglike(args)
+    if args.mode == "nuts_launch":
+        return main_nuts_launch(args)
     if args.workload == "batch64":
         return main_batch(args)
 
@@ -553,13 +603,31 @@ def main():
             t_o += e0.elapsed_time(e1)
             ev_o += sum(r["n_leapfrog"] for r in rec)
             lz_o.append(lnz)
-        se_m = np.std(lnzs, ddof=1) / math.sqrt(len(lnzs)) if len(lnzs) > 1 else float("nan")
+        # the timed runs' ln Z plus untimed runs of the same precision (keys continuing), so that each side of
+        # the 2-sigma comparison has at least --lnz-runs runs
+        lz_m = [float(x) for x in lnzs]
+        for k in range(args.steps, args.lnz_runs):
+            lz_m.append(one_run(multirank.run_key(20_000, rank, k), args.precision, timing=False)[0])
+        se_m = np.std(lz_m, ddof=1) / math.sqrt(len(lz_m)) if len(lz_m) > 1 else float("nan")
         se_f = np.std(lz_o, ddof=1) / math.sqrt(len(lz_o)) if len(lz_o) > 1 else float("nan")
         other = {"fp64_value": ev_o / (t_o * 1e-3), "fp64_ms_per_step": t_o / args.fp64_steps,
                  "speedup_mixed_over_fp64": value / world / (ev_o / (t_o * 1e-3)),
-                 "lnz_mixed": [float(x) for x in lnzs], "lnz_fp64": [float(x) for x in lz_o],
-                 "dlnz": float(np.mean(lnzs) - np.mean(lz_o)),
+                 "lnz_mixed": lz_m, "lnz_fp64": [float(x) for x in lz_o],
+                 "dlnz": float(np.mean(lz_m) - np.mean(lz_o)),
                  "two_sigma": float(2.0 * math.sqrt(se_m ** 2 + se_f ** 2))}
+        gold = os.path.join(ROOT, "tests", "golden", f"lnz_{w.name}_oracle.json")
+        if os.path.exists(gold) and world == 1:
+            # ln Z of the oracle's own full runs on this event (stored by tests/golden/make_lnz_oracle.py; the
+            # same injection and noise, its waveform from the oracle instead of the library: ~1e-12 apart)
+            with open(gold) as fh:
+                ref = [r["lnz"] for r in json.load(fh)["runs"]]
+            se_r = np.std(ref, ddof=1) / math.sqrt(len(ref))
+            other["vs_oracle"] = {
+                "oracle_runs": len(ref), "oracle_mean": float(np.mean(ref)),
+                "dlnz_mixed": float(np.mean(lz_m) - np.mean(ref)),
+                "two_sigma_mixed": float(2.0 * math.sqrt(se_m ** 2 + se_r ** 2)),
+                "dlnz_fp64": float(np.mean(lz_o) - np.mean(ref)),
+                "two_sigma_fp64": float(2.0 * math.sqrt(se_f ** 2 + se_r ** 2))}
 
     # end to end through the public API with host buffers
     e2e = None

@@ -101,7 +101,8 @@ def test_nuts_tick_limit_reports_timeout(precision):
     ctx.clear_status()
     ctx.set_nuts_tick_limit(3)
     t, l, g = G.to_dev(th0), lnl0.clone(), g0.clone()
-    st = api.Context.stats_to_numpy(ctx.nuts_mutate(0.5, t, l, g, None, 0.05, 5, 2, key=5, ctr=1,
+    # a short step: trees grow to the depth limit (31 leapfrogs a transition), far beyond the bound
+    st = api.Context.stats_to_numpy(ctx.nuts_mutate(0.5, t, l, g, None, 2e-5, 5, 2, key=5, ctr=1,
                                                     precision=precision))
     assert ctx.status() == _lib.ETIMEOUT
     th = t.cpu().numpy()
@@ -114,10 +115,10 @@ def test_nuts_tick_limit_reports_timeout(precision):
     ctx.clear_status()
     ctx.set_nuts_tick_limit(0)
     t, l, g = G.to_dev(th0), lnl0.clone(), g0.clone()
-    st = api.Context.stats_to_numpy(ctx.nuts_mutate(0.5, t, l, g, None, 0.05, 5, 2, key=5, ctr=1,
+    st = api.Context.stats_to_numpy(ctx.nuts_mutate(0.5, t, l, g, None, 2e-5, 5, 2, key=5, ctr=1,
                                                     precision=precision))
     assert ctx.status() == 0
-    assert st["n_leapfrog"].max() > 4
+    assert st["n_leapfrog"].max() > 8
 
 
 def test_stage_records_carry_running_lnz():

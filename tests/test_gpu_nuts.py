@@ -8,6 +8,8 @@ likelihood): at least 95 % of particles (99 % on Gaussian targets) must match
 to 1e-7 in prior-width units with identical leapfrog counts, and every
 returned (theta, ln L, grad) must be self-consistent.
 """
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -243,3 +245,43 @@ def test_nuts_bbh11_full_launch_sampled_parity():
     for f, tol in (("n_leapfrog", 0.1), ("accept_sum", 0.1), ("n_divergent", 0.25)):
         a, b = stm[f].astype(float).mean(), st64[f].astype(float).mean()
         assert abs(a - b) <= tol * b + 1e-3, (f, a, b)
+
+
+def test_mixed_state_machine_energy_error_against_fp64():
+    """The mixed path's NUTS state machine keeps momenta, velocities and log-weights in FP32 (positions and
+    the potential energy in FP64). Its effect on the energy check, measured: from the same 2048 starts near
+    the injection of the 11-D workload, one leapfrog per transition (max depth 1, so the acceptance statistic
+    is min(1, e^-dH)), the mixed and FP64 kernels' energy errors dH agree to 1e-3 (four times the mixed path's
+    ln L budget, which dominates: FP32 momenta move the kinetic energy by ~1e-6) at every particle where
+    both are below 20; with full trees (depth 6, two transitions) the mean acceptance statistic, mean depth
+    and leapfrog count agree within their Monte Carlo spread."""
+    G.require_gpu()
+    w = inputs.bbh11()
+    ev, ctx, th_inj, _ = G.event_pair(w)
+    n = 2048
+    th = inputs.ball(w, th_inj, n, 21, rel=1e-3)
+    t0 = G.to_dev(th)
+    l0, g0 = ctx.loglike_grad(t0, "fp64")
+    eps0 = float(np.min(np.std(th, axis=0)))
+    for scale in (0.05, 0.3):
+        dh = {}
+        for prec in ("fp64", "mixed"):
+            t, l, g = t0.clone(), l0.clone(), g0.clone()
+            st = api.Context.stats_to_numpy(ctx.nuts_mutate(1.0, t, l, g, None, scale * eps0, 1, 1, key=31, ctr=2,
+                                                            precision=prec))
+            assert np.all(st["n_leapfrog"] == 1)
+            acc = st["accept_sum"]
+            dh[prec] = np.where(acc < 1.0, -np.log(np.maximum(acc, 1e-300)), 0.0)
+        both = (dh["fp64"] < 20.0) & (dh["mixed"] < 20.0) & (dh["fp64"] > 0.0) & (dh["mixed"] > 0.0)
+        assert both.sum() > 100
+        assert np.max(np.abs(dh["mixed"][both] - dh["fp64"][both])) <= 1e-3
+    stats_by = {}
+    for prec in ("fp64", "mixed"):
+        t, l, g = t0.clone(), l0.clone(), g0.clone()
+        stats_by[prec] = api.Context.stats_to_numpy(ctx.nuts_mutate(1.0, t, l, g, None, 0.5 * eps0, 6, 2, key=32,
+                                                                    ctr=3, precision=prec))
+    for f in ("accept_sum", "depth_sum", "n_leapfrog"):
+        a, b = stats_by["fp64"][f] / 2.0, stats_by["mixed"][f] / 2.0
+        spread = 3.0 * math.sqrt(np.var(a) / n + np.var(b) / n)
+        assert abs(np.mean(a) - np.mean(b)) <= spread + 1e-3, (f, np.mean(a), np.mean(b), spread)
+    assert ctx.status() == 0
