@@ -416,6 +416,13 @@ __device__ void prologue_phase(const DevModel& m, const DevEvent& ev, const doub
 #pragma unroll
     for (int j = 0; j < kNPn; ++j) split2(sc.alpha[j], &sc.ahi[j], &sc.alo[j]);
     sc.c0f = (float)(sc.c0 - rint(sc.c0));
+  } else if constexpr (!std::is_same<DT, double>::value) {
+    // the mixed sweep's FP32-pair terms take the double-float values as they are
+#pragma unroll
+    for (int j = 0; j < kNPn; ++j) {
+      sc.ahi[j] = alpha[j].v.hi;
+      sc.alo[j] = alpha[j].v.lo;
+    }
   }
 }
 

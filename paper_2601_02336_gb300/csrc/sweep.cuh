@@ -12,9 +12,12 @@
 //                  each product's integer turns are removed exactly (FMA error
 //                  term kept), the fraction stays in [-1/2, 1/2]; no FP64 in
 //                  the bin loop (worst-case phase error ~3e-7 turns).
-//   SHARPY_MIXED : the post-Newtonian polynomial accumulated in FP64 on top
-//                  of the offset 1.5 * 2^20 turns, whose low mantissa word is
-//                  its fractional turn in 2^-32 units; the delay term f tau_a
+//   SHARPY_MIXED : the post-Newtonian terms that carry the large phase
+//                  (x^5, x^3, x^2, ln f) accumulated in FP64 on top of the
+//                  offset 1.5 * 2^20 turns, whose low mantissa word is their
+//                  fractional turn in 2^-32 units; the four terms below ~8
+//                  turns (x, y, y ln f, y^2) in FP32 pairs as in the split
+//                  path, added in 32-bit fixed point; the delay term f tau_a
 //                  of each detector in FP32 from hi/lo splits (exact FMA error
 //                  term, fraction added in 32-bit fixed point); FP32 sincos,
 //                  carrier and moments. Per-lane FP32 partial sums are flushed
@@ -27,6 +30,10 @@
 namespace sharpy {
 
 constexpr int kFlush = 64;  // lane iterations per FP32 block
+// The mixed sweep's split of the post-Newtonian basis: terms accumulated in
+// FP64 (x^5, x^3, x^2, ln f) and terms formed in FP32 pairs (x, y, y ln f, y^2).
+__host__ __device__ constexpr int large_pn(int i) { return i < 3 ? i : 4; }
+__host__ __device__ constexpr int small_pn(int i) { return i == 0 ? 3 : i + 4; }
 
 template <int NDET, bool GRAD>
 struct MomCount {
@@ -135,12 +142,10 @@ __device__ void sweep_mixed(const DevEvent& ev, const SweepCoef& sc, float* mom)
   for (int j = 0; j < kNPn; ++j) al[j] = sc.alpha[j];
   const double s0 = sc.c0 + kTurnOffset;
   float ah[kNPn], alo[kNPn], th[NDET], tl[NDET];
-  if (SPLIT) {
 #pragma unroll
-    for (int j = 0; j < kNPn; ++j) {
-      ah[j] = sc.ahi[j];
-      alo[j] = sc.alo[j];
-    }
+  for (int j = 0; j < kNPn; ++j) {
+    ah[j] = sc.ahi[j];
+    alo[j] = sc.alo[j];
   }
 #pragma unroll
   for (int a = 0; a < NDET; ++a) {
@@ -158,6 +163,8 @@ __device__ void sweep_mixed(const DevEvent& ev, const SweepCoef& sc, float* mom)
 #pragma unroll
       for (int j = 0; j < kNBasis; ++j) bf[j] = __ldg(ev.b32 + (int64_t)j * K + k);
     } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) bf[small_pn(i)] = __ldg(ev.b32 + (int64_t)small_pn(i) * K + k);
       bf[8] = __ldg(ev.b32 + (int64_t)8 * K + k);
     }
     const float fl = __ldg(ev.b32lo + (int64_t)8 * K + k);
@@ -166,9 +173,28 @@ __device__ void sweep_mixed(const DevEvent& ev, const SweepCoef& sc, float* mom)
     int turn_s = 0;
     float F = 0.0f, Sm = 0.0f;
     if (!SPLIT) {
+      // the four terms that carry the large phase (Newtonian, 1PN, 1.5PN and
+      // the 2.5PN logarithm: up to ~2e3 turns on the long segment) accumulated
+      // in FP64 on the offset
 #pragma unroll
-      for (int j = 0; j < kNPn; ++j) S = fma(al[j], __ldg(ev.b64 + (int64_t)j * K + k), S);
-      turn_s = __double2loint(S);  // fractional turn of the polynomial, 2^-32 units
+      for (int i = 0; i < 4; ++i) S = fma(al[large_pn(i)], __ldg(ev.b64 + (int64_t)large_pn(i) * K + k), S);
+      turn_s = __double2loint(S);  // fractional turn of the large terms, 2^-32 units
+      // the four terms below ~8 turns (2PN, 3PN, its logarithm, 3.5PN) in FP32
+      // pairs: each product's integer turns removed exactly (FMA error term
+      // kept), the fractions summed pairwise in [-1/2, 1/2], then added to the
+      // FP64 part in 32-bit fixed point
+      float fr[4], er[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int j = small_pn(i);
+        const float bl = __ldg(ev.b32lo + (int64_t)j * K + k);
+        const float p = __fmul_rn(ah[j], bf[j]);
+        fr[i] = frac_turn(p);
+        er[i] = fmaf(ah[j], bl, fmaf(alo[j], bf[j], fmaf(ah[j], bf[j], -p)));
+      }
+      const float f = frac_turn(__fadd_rn(frac_turn(__fadd_rn(fr[0], fr[1])), frac_turn(__fadd_rn(fr[2], fr[3]))));
+      const float q = frac_turn(__fadd_rn(f, __fadd_rn(__fadd_rn(er[0], er[1]), __fadd_rn(er[2], er[3]))));
+      turn_s += __float2int_rn(q * 4294967296.0f);  // wraps mod 1 turn
     } else {
       // sum_j alpha_j B_j mod 1: p = ahi*bhi is exact up to e (FMA), its integer
       // part is removed exactly; the fractions are summed pairwise, reduced to
