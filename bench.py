@@ -383,6 +383,31 @@ def main_nuts_launch(args):
     return 0
 
 
+def main_loglike_launch(args):
+    """One sharpy_loglike_grad call (ln L + gradient) on N vectors near the injection of a workload (sigma 1e-3 of
+    the prior width), after one untimed call: the command the standalone likelihood kernel's instruction-count
+    capture is taken on (--workload, --precision, --particles)."""
+    import torch
+
+    from paper_2601_02336_gb300 import api, inputs
+    torch.cuda.set_device(0)
+    w = inputs.WORKLOADS[args.workload]()
+    ctx, th_inj, _ = api.make_event(w, seed=0)
+    n = args.particles or w.n_particles
+    th = torch.tensor(inputs.ball(w, th_inj, n, 2, rel=1e-3), dtype=torch.float64, device="cuda")
+    ctx.loglike_grad(th, args.precision)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.loglike_grad(th, args.precision)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    act = float(_active_bins(w, th.cpu().numpy()).sum())
+    print(json.dumps({"mode": "loglike_launch", "workload": w.name, "precision": args.precision, "particles": n,
+                      "ms": e0.elapsed_time(e1), "active_bin_det": act, "status": ctx.status()}))
+    return 0
+
+
 def main_batch(args):
     """64 uneven events (4/8/16/32 s segments, 512-8192 particles, NUTS depth 8)
     sampled together by the batched driver: one step = one batched run of all
@@ -481,7 +506,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="bbh11", choices=["tiny", "bbh11", "bbh11_long", "bns", "batch64"])
-    ap.add_argument("--mode", default="smc", choices=["smc", "loglike", "nuts_launch"])
+    ap.add_argument("--mode", default="smc", choices=["smc", "loglike", "nuts_launch", "loglike_launch"])
+    ap.add_argument("--particles", type=int, default=0, help="loglike_launch: vectors per call (0: the workload's)")
     ap.add_argument("--ensemble", default=None, choices=["first", "late"], help="nuts_launch: one ensemble only")
     ap.add_argument("--slots", type=int, default=0, choices=[0, 8, 16, 32],
                     help="batch64: NUTS particles per CTA (0: autotuned)")
@@ -494,6 +520,8 @@ def main():
         return main_loglike(args)
     if args.mode == "nuts_launch":
         return main_nuts_launch(args)
+    if args.mode == "loglike_launch":
+        return main_loglike_launch(args)
     if args.workload == "batch64":
         return main_batch(args)
 

@@ -69,6 +69,8 @@ _SIGS = {
     "sharpy_prior_sample": (C.c_int, [_CTX, C.c_int64, _VP, C.c_uint64, C.c_uint64, _VP]),
     "sharpy_prior_logpdf_grad": (C.c_int, [_CTX, C.c_int64, _VP, _VP, _VP, _VP]),
     "sharpy_loglike_grad": (C.c_int, [_CTX, C.c_int64, _VP, _VP, _VP, C.c_int, _VP]),
+    "sharpy_loglike_split": (C.c_int, [_CTX, C.c_int64, C.c_int, C.c_int]),
+    "sharpy_set_loglike_split": (C.c_int, [_CTX, C.c_int]),
     "sharpy_waveform": (C.c_int, [_CTX, C.c_int64, _VP, _VP, _VP]),
     "sharpy_nuts_mutate": (C.c_int, [_CTX, C.c_int64, C.c_double, _VP, _VP, _VP, _VP, C.c_double,
                                      C.c_int, C.c_int, C.c_uint64, C.c_uint64, C.c_int, _VP, _VP]),

@@ -123,6 +123,14 @@ class Context:
                                         _stream()), "sharpy_loglike_grad")
         return lnl, g
 
+    def loglike_split(self, n, precision="mixed", grad=True):
+        """Warps per vector the likelihood call's tuner picked for n vectors (0: not tuned yet)."""
+        return lib().sharpy_loglike_split(self._h, int(n), _prec(precision), 1 if grad else 0)
+
+    def set_loglike_split(self, split):
+        """Force 1, 2, 4 or 8 warps per vector in later likelihood calls (0: tune)."""
+        check(lib().sharpy_set_loglike_split(self._h, int(split)), "sharpy_set_loglike_split")
+
     def waveform(self, theta):
         theta = _dev(theta, "theta")
         h = torch.empty((theta.shape[0], self.n_det, self.n_bins, 2), dtype=torch.float64,

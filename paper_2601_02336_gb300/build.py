@@ -15,13 +15,15 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsharpy.so")
 # (source, extra nvcc flags, object tag): nuts_inst.cu is compiled once per
-# (precision, detector count) so the persistent-kernel variants build in parallel.
+# (precision, detector count) and loglike_inst.cu once per precision, so the
+# kernel variants build in parallel.
 UNITS = [("context.cu", [], "context"), ("loglike.cu", [], "loglike"), ("smc.cu", [], "smc"),
          ("nuts.cu", [], "nuts"), ("run.cu", [], "run"), ("probe.cu", [], "probe"),
          ("batch.cu", [], "batch"), ("recycle.cu", [], "recycle"),
          ("metric.cu", [], "metric")] + [
     ("nuts_inst.cu", [f"-DSHARPY_NUTS_PREC={p}", f"-DSHARPY_NUTS_NDET={d}"], f"nuts_p{p}_{d}")
-    for p in (0, 1, 2) for d in (1, 2, 3)]
+    for p in (0, 1, 2) for d in (1, 2, 3)] + [
+    ("loglike_inst.cu", [f"-DSHARPY_LL_PREC={p}"], f"loglike_p{p}") for p in (0, 1, 2)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "-Xptxas", "-O3"]
 

@@ -6,6 +6,21 @@
 
 #include "common.cuh"
 
+// Key of the likelihood call's tuned split factor.
+struct LoglikeTuneKey {
+  int64_t n_bins;
+  int n_det;
+  int64_t n;
+  int precision, grad;
+  bool operator==(const LoglikeTuneKey& o) const {
+    return n_bins == o.n_bins && n_det == o.n_det && n == o.n && precision == o.precision && grad == o.grad;
+  }
+};
+struct LoglikeTuned {
+  LoglikeTuneKey key;
+  int split;
+};
+
 struct sharpy_ctx {
   int device = 0;
   sharpy::DevModel model{};
@@ -39,6 +54,9 @@ struct sharpy_ctx {
   int64_t nuts_tick_limit = 0;
   int64_t first_id = 0;         // ensemble index of row 0 of the particle arrays (sharpy_set_shard)  // > 0: lowered NUTS tick bound (sharpy_set_nuts_tick_limit)
   int tuned_slots[3][2] = {};
+  // likelihood kernel: warps per particle picked per call shape (loglike.cu)
+  std::vector<LoglikeTuned> ll_tuned;
+  int ll_split_forced = 0;  // > 0: every likelihood call uses this split (sharpy_set_loglike_split)
   int64_t tuned_n[3][2] = {{-1, -1}, {-1, -1}, {-1, -1}};
 };
 

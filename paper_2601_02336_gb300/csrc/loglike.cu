@@ -1,71 +1,14 @@
 // sharpy_loglike_grad, sharpy_waveform, sharpy_prior_* : kernels and entry points.
 //
-// Likelihood launch shape: one CTA of kWarps warps handles kWarps particles.
-// Warp 0 computes the per-particle prologue lane-parallel (lane s = particle
-// s of the CTA), every warp then sweeps the bins of one particle, and warp 0
-// finishes with the lane-parallel epilogue. The FP64 scalar work thus runs
-// on kWarps lanes per instruction instead of one.
+// The likelihood kernel itself is in loglike_kernel.cuh.
 #include <cstdio>
 
-#include "context.cuh"
-#include "sweep.cuh"
+#include "loglike_kernel.cuh"
+#include "tune.cuh"
 
 using namespace sharpy;
 
 namespace sharpy {
-
-constexpr int kWarps = 8;
-
-template <int PREC, bool GRAD, int NDET>
-__global__ void __launch_bounds__(kWarps * 32)
-loglike_kernel(DevModel m, DevEvent ev, int64_t n, const double* __restrict__ theta, double* __restrict__ lnl,
-               double* __restrict__ grad, int* status) {
-  using DT = typename std::conditional<PREC == SHARPY_FP64, double, float>::type;
-  __shared__ SweepCoef sc[kWarps];
-  __shared__ EpiCoef<DT> ec[kWarps];
-  using MT = typename MomType<PREC>::type;
-  __shared__ MT mom[kWarps][NDET * kNMom * 2];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t base = (int64_t)blockIdx.x * kWarps;
-  const int D = m.n_dim;
-  if (warp == 0 && lane < kWarps) {
-    int64_t p = base + lane;
-    if (p < n) {
-      double th[kMaxDim];
-      for (int i = 0; i < D; ++i) th[i] = theta[p * D + i];
-      prologue<DT, GRAD, PREC == SHARPY_MIXED_SPLIT>(m, ev, th, sc[lane], ec[lane]);
-    } else {
-      sc[lane].ok = 0;
-      sc[lane].kisco = -1;
-    }
-  }
-  __syncthreads();
-  {
-    int64_t p = base + warp;
-    MT* mw = mom[warp];
-    for (int i = lane; i < NDET * kNMom * 2; i += 32) mw[i] = MT(0);
-    __syncwarp();
-    if (p < n && sc[warp].ok) sweep<PREC, GRAD, NDET>(ev, sc[warp], mw);
-  }
-  __syncthreads();
-  if (warp == 0 && lane < kWarps) {
-    int64_t p = base + lane;
-    if (p < n) {
-      double l = NAN, gph[SHARPY_NPHYS];
-      if (sc[lane].ok) epilogue<DT, GRAD>(ev, sc[lane], ec[lane], mom[lane], &l, gph);
-      lnl[p] = l;
-      bool fin = isfinite(l);
-      if (GRAD) {
-        for (int i = 0; i < D; ++i) {
-          double g = sc[lane].ok ? gph[m.phys[i]] : NAN;
-          grad[p * D + i] = g;
-          fin = fin && isfinite(g);
-        }
-      }
-      if (!fin) set_status(status, SHARPY_ENONFINITE);
-    }
-  }
-}
 
 __global__ void gaussmix_kernel(DevModel m, int64_t n, const double* __restrict__ theta, double* __restrict__ lnl,
                                 double* __restrict__ grad) {
@@ -143,15 +86,37 @@ __global__ void prior_logpdf_kernel(DevModel m, int64_t n, const double* __restr
     for (int i = 0; i < m.n_dim; ++i) glp[p * m.n_dim + i] = g[i];
 }
 
+// The split factor for this call: the context's tuned choice for (bins,
+// detectors, particles, precision, gradient), else every candidate is timed
+// on this call (one untimed and one timed launch each; the outputs are the
+// same for every candidate) and the fastest is kept.
 template <int PREC, bool GRAD>
-static cudaError_t launch_ll(sharpy_ctx* c, int64_t n, const double* th, double* lnl, double* grad, cudaStream_t s) {
-  dim3 grid((unsigned)((n + kWarps - 1) / kWarps));
-  switch (c->ev.n_det) {
-    case 1: loglike_kernel<PREC, GRAD, 1><<<grid, kWarps * 32, 0, s>>>(c->model, c->ev, n, th, lnl, grad, c->d_status); break;
-    case 2: loglike_kernel<PREC, GRAD, 2><<<grid, kWarps * 32, 0, s>>>(c->model, c->ev, n, th, lnl, grad, c->d_status); break;
-    default: loglike_kernel<PREC, GRAD, 3><<<grid, kWarps * 32, 0, s>>>(c->model, c->ev, n, th, lnl, grad, c->d_status); break;
-  }
-  return cudaGetLastError();
+static cudaError_t launch_ll_prec(sharpy_ctx* c, int split, int64_t n, const double* th, double* lnl, double* grad,
+                                 cudaStream_t s) {
+  if (PREC == SHARPY_FP64) return launch_ll_p0(c, GRAD, split, n, th, lnl, grad, s);
+  if (PREC == SHARPY_MIXED) return launch_ll_p1(c, GRAD, split, n, th, lnl, grad, s);
+  return launch_ll_p2(c, GRAD, split, n, th, lnl, grad, s);
+}
+
+template <int PREC, bool GRAD>
+static int launch_ll(sharpy_ctx* c, int64_t n, const double* th, double* lnl, double* grad, cudaStream_t s) {
+  if (c->ll_split_forced > 0)
+    return launch_ll_prec<PREC, GRAD>(c, c->ll_split_forced, n, th, lnl, grad, s) == cudaSuccess ? SHARPY_OK
+                                                                                              : SHARPY_ECUDA;
+  const LoglikeTuneKey key{c->ev.n_bins, c->ev.n_det, n, PREC, GRAD ? 1 : 0};
+  for (const auto& e : c->ll_tuned)
+    if (e.key == key) return launch_ll_prec<PREC, GRAD>(c, e.split, n, th, lnl, grad, s) == cudaSuccess
+                                 ? SHARPY_OK : SHARPY_ECUDA;
+  TuneCandidate cands[kNumSplitChoices];
+  for (int i = 0; i < kNumSplitChoices; ++i) cands[i].slots = kSplitChoices[i];
+  auto trial = [&](int split, cudaStream_t ts) -> int {
+    return launch_ll_prec<PREC, GRAD>(c, split, n, th, lnl, grad, ts) == cudaSuccess ? SHARPY_OK : SHARPY_ECUDA;
+  };
+  int best = 1;
+  const int rc = tune_slots(cands, kNumSplitChoices, trial, s, &best);
+  if (rc) return rc;
+  c->ll_tuned.push_back({key, best});
+  return SHARPY_OK;
 }
 
 }  // namespace sharpy
@@ -174,14 +139,32 @@ int sharpy_loglike_grad(sharpy_ctx* c, int64_t n, const double* theta, double* l
     gaussmix_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(c->model, n, theta, lnl, grad);
     e = cudaGetLastError();
   } else if (precision == SHARPY_FP64) {
-    e = grad ? launch_ll<SHARPY_FP64, true>(c, n, theta, lnl, grad, s) : launch_ll<SHARPY_FP64, false>(c, n, theta, lnl, grad, s);
+    return grad ? launch_ll<SHARPY_FP64, true>(c, n, theta, lnl, grad, s) : launch_ll<SHARPY_FP64, false>(c, n, theta, lnl, grad, s);
   } else if (precision == SHARPY_MIXED) {
-    e = grad ? launch_ll<SHARPY_MIXED, true>(c, n, theta, lnl, grad, s) : launch_ll<SHARPY_MIXED, false>(c, n, theta, lnl, grad, s);
+    return grad ? launch_ll<SHARPY_MIXED, true>(c, n, theta, lnl, grad, s)
+                : launch_ll<SHARPY_MIXED, false>(c, n, theta, lnl, grad, s);
   } else {
-    e = grad ? launch_ll<SHARPY_MIXED_SPLIT, true>(c, n, theta, lnl, grad, s)
-             : launch_ll<SHARPY_MIXED_SPLIT, false>(c, n, theta, lnl, grad, s);
+    return grad ? launch_ll<SHARPY_MIXED_SPLIT, true>(c, n, theta, lnl, grad, s)
+                : launch_ll<SHARPY_MIXED_SPLIT, false>(c, n, theta, lnl, grad, s);
   }
   return e == cudaSuccess ? SHARPY_OK : SHARPY_ECUDA;
+}
+
+int sharpy_set_loglike_split(sharpy_ctx* c, int split) {
+  int rc = check_ctx(c, false);
+  if (rc) return rc;
+  if (split != 0 && split != 1 && split != 2 && split != 4 && split != 8) return SHARPY_EINVAL;
+  c->ll_split_forced = split;
+  return SHARPY_OK;
+}
+
+int sharpy_loglike_split(sharpy_ctx* c, int64_t n, int precision, int with_grad) {
+  int rc = check_ctx(c, true);
+  if (rc) return rc;
+  const LoglikeTuneKey key{c->ev.n_bins, c->ev.n_det, n, precision, with_grad ? 1 : 0};
+  for (const auto& e : c->ll_tuned)
+    if (e.key == key) return e.split;
+  return 0;
 }
 
 int sharpy_waveform(sharpy_ctx* c, int64_t n, const double* theta, double* h, sharpy_stream stream) {

@@ -31,6 +31,10 @@ int launch_nuts(int precision, int ndet, int slots, const NutsArgs& A, unsigned 
   if (ndet == 2) return launch_nuts_p2_2(slots, A, grid, s);
   return launch_nuts_p2_3(slots, A, grid, s);
 }
+// Segments of at least this many bins (the 128 s BNS workload) spread each
+// long sweep's streams over the warps of a NUTS tick.
+constexpr int64_t kLongSignalBins = 65536;
+
 // slots: particles per CTA; 0 picks the autotuned count for (n, precision) if
 // the context has one, else the widest count that still gives about two CTAs
 // per SM.
@@ -58,6 +62,7 @@ int enqueue_nuts(sharpy_ctx* c, int64_t n, const double* beta_ptr, double beta, 
   A.status = c->d_status;
   A.tick_limit = c->nuts_tick_limit;
   A.id_offset = c->first_id;
+  A.stream_part = nullptr;
   const int lm = pminv ? 1 : 0;
   if (!slots && c->tuned_slots[precision][lm] && c->tuned_n[precision][lm] == n) slots = c->tuned_slots[precision][lm];
   if (!slots) {
@@ -67,6 +72,13 @@ int enqueue_nuts(sharpy_ctx* c, int64_t n, const double* beta_ptr, double beta, 
     slots = n >= (int64_t)16 * 2 * sms * 3 / 4 ? 16 : 8;
   }
   const int nd = c->model.model == SHARPY_MODEL_TAYLORF2 ? c->ev.n_det : 1;
+  if (c->model.model == SHARPY_MODEL_TAYLORF2 && c->ev.n_bins >= kLongSignalBins) {
+    // long signals: the sweeps' streams spread over the warps of a tick
+    const int64_t rows = (n + slots - 1) / slots * slots;
+    const int rc = ensure_scratch(c, (size_t)rows * kStreams * 64 * sizeof(double));
+    if (rc) return rc;
+    A.stream_part = (double*)c->d_scratch;
+  }
   A.pminv = pminv;
   A.pchol = pchol;
   A.local_metric = pminv ? 1 : 0;

@@ -86,6 +86,10 @@ struct NutsArgs {
   int* status;
   int64_t tick_limit;      // > 0: lowered tick bound (failure-detection tests); 0: the default
   int64_t id_offset;       // ensemble index of row 0: names the rows' random numbers (a shard of an ensemble)
+  // long signals (null otherwise): per-stream moment sums of every slot,
+  // [CTA][slot][kStreams][64] doubles, so that a sweep's streams can run on
+  // several warps of the tick
+  double* stream_part;
   // batched driver (null otherwise): CTA b runs block cta_map[b].y of event
   // cta_map[b].x, whose arguments are batch[cta_map[b].x]; an event's CTAs
   // return at once while *active == 0, and its counter is *stage << 8
@@ -136,7 +140,11 @@ struct NutsShared {
   int pending[SLOTS];
   int order[SLOTS];  // this tick's sweeps, longest (largest k_ISCO) first
   int n_order;
-  int next;          // next entry of order to claim
+  int next;          // next entry of order (or of items) to claim
+  // long signals: the tick's sweep work items in claiming order, slot * 16 +
+  // stream + 1 (stream -1: the slot's whole sweep)
+  short items[SLOTS * kStreams];
+  int n_items;
   int cslot[SLOTS];  // this tick's state machine of lane group g: slot cslot[g], or -1
   Slot<VT> sstate[SLOTS];
 };
@@ -801,6 +809,22 @@ __global__ void __launch_bounds__(kNutsWarps * 32, PREC == SHARPY_FP64 ? 2 : 3)
         S.n_order = __popc(sweeps);
         S.next = 0;
       }
+      if (A.stream_part) {
+        // a sweep of more than one chunk becomes its kStreams streams, each a
+        // work item, longest sweeps first
+        __syncwarp();
+        if (lane == 0) {
+          int ni = 0;
+          for (int r = 0; r < S.n_order; ++r) {
+            const int slot = S.order[r];
+            if (sc[slot].kisco >= kChunkBins)
+              for (int st = 0; st < kStreams; ++st) S.items[ni++] = (short)(slot * 16 + st + 1);
+            else
+              S.items[ni++] = (short)(slot * 16);
+          }
+          S.n_items = ni;
+        }
+      }
     }
     if (warp == cw) {
       // this tick's state machines, one per warp before a second one on any
@@ -818,7 +842,7 @@ __global__ void __launch_bounds__(kNutsWarps * 32, PREC == SHARPY_FP64 ? 2 : 3)
     // (B) sweeps: each warp claims the next sweep of the longest-first order
     // (a sweep writes all its moments; the warp that runs it does not change
     // the result)
-    if (gw) {
+    if (gw && !A.stream_part) {
       for (;;) {
         int k = 0;
         if (lane == 0) k = atomicAdd(&S.next, 1);
@@ -826,6 +850,35 @@ __global__ void __launch_bounds__(kNutsWarps * 32, PREC == SHARPY_FP64 ? 2 : 3)
         if (k >= S.n_order) break;
         const int slot = S.order[k];
         sweep<PREC, true, NDET>(A.ev, sc[slot], mom[slot]);
+      }
+    } else if (gw) {
+      // long signals: whole short sweeps, and the streams of the long ones
+      // with their sums stored per stream (merged in stream order below)
+      constexpr int NACC = MomCount<NDET, true>::value;
+      using FS = FlushShape<NACC>;
+      for (;;) {
+        int k = 0;
+        if (lane == 0) k = atomicAdd(&S.next, 1);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= S.n_items) break;
+        const int item = S.items[k];
+        const int slot = item >> 4, st = (item & 15) - 1;
+        if (st < 0) {
+          sweep<PREC, true, NDET>(A.ev, sc[slot], mom[slot]);
+          continue;
+        }
+        double v[FS::KEEP];
+        if constexpr (PREC == SHARPY_FP64) {
+          fp64_stream<true, NDET>(A.ev, sc[slot], st, v);
+        } else {
+          float hi[FS::KEEP], lo[FS::KEEP];
+          mixed_stream<true, NDET, PREC == SHARPY_MIXED_SPLIT>(A.ev, sc[slot], st, hi, lo);
+#pragma unroll
+          for (int t = 0; t < FS::KEEP; ++t) v[t] = (double)hi[t] + (double)lo[t];
+        }
+        double* part = A.stream_part + (((int64_t)blockIdx.x * SLOTS + slot) * kStreams + st) * 64;
+#pragma unroll
+        for (int t = 0; t < FS::KEEP; ++t) part[lane * FS::KEEP + t] = v[t];
       }
     }
     __syncthreads();
@@ -835,6 +888,17 @@ __global__ void __launch_bounds__(kNutsWarps * 32, PREC == SHARPY_FP64 ? 2 : 3)
     // slot does not change what it computes
     const int cs = S.cslot[warp * SPW + lane / G];
     if (cs >= 0) {
+      if (gw && A.stream_part && sc[cs].ok && sc[cs].kisco >= kChunkBins) {
+        // the slot's streams, in stream order (the sum sweep() forms on one warp)
+        constexpr int NACC = MomCount<NDET, true>::value;
+        const double* part = A.stream_part + ((int64_t)blockIdx.x * SLOTS + cs) * kStreams * 64;
+        for (int idx = tg; idx < NACC; idx += G) {
+          double tot = 0.0;
+          for (int st = 0; st < kStreams; ++st) tot += part[st * 64 + idx];
+          mom[cs][acc_to_mom<NDET, true>(idx)] = (MT)tot;
+        }
+        __syncwarp(gmask);
+      }
       Slot<VT> sl = S.sstate[cs];
       NT nu(A, S, cs, tg, gmask);
       VT gl_new[DPL], glp_new[DPL];

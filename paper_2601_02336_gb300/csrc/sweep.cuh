@@ -30,6 +30,12 @@
 namespace sharpy {
 
 constexpr int kFlush = 64;  // lane iterations per FP32 block
+// Long sweeps are cut into chunks of kFlush lane iterations (2048 bins) dealt
+// to kStreams streams (chunk c to stream c mod kStreams); a stream's result
+// does not depend on which warp computes it, and streams are merged in a fixed
+// order, so any number of warps per particle gives the same moments.
+constexpr int kChunkBins = kFlush * 32;
+constexpr int kStreams = 8;
 // The mixed sweep's split of the post-Newtonian basis: terms accumulated in
 // FP64 (x^5, x^3, x^2, ln f) and terms formed in FP32 pairs (x, y, y ln f, y^2).
 __host__ __device__ constexpr int large_pn(int i) { return i < 3 ? i : 4; }
@@ -125,14 +131,17 @@ __device__ __forceinline__ float frac_turn(float x) {
   return __fsub_rn(x, __fsub_rn(__fadd_rn(x, kRound32), kRound32));
 }
 
+// One stream of a mixed sweep: the chunks c = s, s + kStreams, ... of 2048
+// bins (64 lane iterations: one FP32 block each) below k_ISCO, accumulated
+// into this lane's compensated outer sums hi, lo (kept lane-distributed as
+// the flush leaves them). Returns whether the stream had any bin.
 template <bool GRAD, int NDET, bool SPLIT>
-__device__ void sweep_mixed(const DevEvent& ev, const SweepCoef& sc, float* mom) {
+__device__ bool mixed_stream(const DevEvent& ev, const SweepCoef& sc, int s, float* hi, float* lo) {
   constexpr int NACC = MomCount<NDET, GRAD>::value;
   constexpr int NOUT = FlushShape<NACC>::KEEP;
   const int lane = threadIdx.x & 31;
   const int64_t K = ev.n_bins;
   float acc[NACC];
-  float hi[NOUT], lo[NOUT];
 #pragma unroll
   for (int i = 0; i < NACC; ++i) acc[i] = 0.0f;
 #pragma unroll
@@ -153,9 +162,13 @@ __device__ void sweep_mixed(const DevEvent& ev, const SweepCoef& sc, float* mom)
     tl[a] = sc.tlo[a];
   }
   const int kend = sc.kisco;
-  int it = 0;
-  // Warp-uniform trip count: lanes past k_ISCO idle but still join the flushes.
-  for (int k0 = 0; k0 <= kend; k0 += 32) {
+  bool any = false;
+  // Warp-uniform trip counts: lanes past k_ISCO idle but still join the flushes.
+  for (int c = s; c * kChunkBins <= kend; c += kStreams) {
+    any = true;
+    for (int it = 0; it < kFlush; ++it) {
+    const int k0 = c * kChunkBins + it * 32;
+    if (k0 > kend) break;
     const int k = k0 + lane;
     if (k <= kend) {
     float bf[kNBasis];
@@ -253,24 +266,56 @@ __device__ void sweep_mixed(const DevEvent& ev, const SweepCoef& sc, float* mom)
       }
     }
     }
-    if (++it == kFlush) {
-      flush<NACC>(acc, hi, lo, lane);
-      it = 0;
     }
+    flush<NACC>(acc, hi, lo, lane);
   }
-  // Every lane takes part in the final flush (warp-uniform).
-  flush<NACC>(acc, hi, lo, lane);
+  return any;
+}
+
+// Moments of one particle on one warp (the NUTS kernel's sweep). A sweep of
+// one chunk (k_ISCO < 2048: every BBH workload here) is its single stream:
+// the moments are hi + lo. Longer sweeps take the kStreams streams in order
+// and add each stream's hi + lo in FP64: the result the likelihood kernel
+// gets from the same streams spread over several warps, bit for bit.
+template <bool GRAD, int NDET, bool SPLIT>
+__device__ void sweep_mixed(const DevEvent& ev, const SweepCoef& sc, float* mom) {
+  constexpr int NACC = MomCount<NDET, GRAD>::value;
+  constexpr int NOUT = FlushShape<NACC>::KEEP;
+  const int lane = threadIdx.x & 31;
+  float hi[NOUT], lo[NOUT];
+  float out[NOUT];
+  if (sc.kisco < kChunkBins) {
+    mixed_stream<GRAD, NDET, SPLIT>(ev, sc, 0, hi, lo);
+#pragma unroll
+    for (int t = 0; t < NOUT; ++t) out[t] = hi[t] + lo[t];
+  } else {
+    double tot[NOUT];
+#pragma unroll
+    for (int t = 0; t < NOUT; ++t) tot[t] = 0.0;
+    for (int st = 0; st < kStreams; ++st) {
+      if (!mixed_stream<GRAD, NDET, SPLIT>(ev, sc, st, hi, lo)) break;
+#pragma unroll
+      for (int t = 0; t < NOUT; ++t) tot[t] += (double)hi[t] + (double)lo[t];
+    }
+#pragma unroll
+    for (int t = 0; t < NOUT; ++t) out[t] = (float)tot[t];
+  }
   if (FlushShape<NACC>::owner(lane)) {
 #pragma unroll
     for (int t = 0; t < NOUT; ++t) {
       const int idx = FlushShape<NACC>::index(lane, t);
-      if (idx < NACC) mom[acc_to_mom<NDET, GRAD>(idx)] = hi[t] + lo[t];
+      if (idx < NACC) mom[acc_to_mom<NDET, GRAD>(idx)] = out[t];
     }
   }
 }
 
+// One stream of the FP64 sweep (chunks c = s, s + kStreams, ... of 2048 bins
+// below k_ISCO): per-lane FP64 sums, then the warp reduce-scatter (the same
+// pairing as a butterfly sum per moment, with NP/2 + NP/4 + ... FP64 adds per
+// lane instead of 5 NP); lane l holds its sums in v. Returns whether the
+// stream had any bin.
 template <bool GRAD, int NDET>
-__device__ void sweep_fp64(const DevEvent& ev, const SweepCoef& sc, double* mom) {
+__device__ bool fp64_stream(const DevEvent& ev, const SweepCoef& sc, int s, double* v_out) {
   constexpr int NACC = MomCount<NDET, GRAD>::value;
   const int lane = threadIdx.x & 31;
   const int64_t K = ev.n_bins;
@@ -281,51 +326,78 @@ __device__ void sweep_fp64(const DevEvent& ev, const SweepCoef& sc, double* mom)
 #pragma unroll
   for (int j = 0; j < kNPn; ++j) al[j] = sc.alpha[j];
   const int kend = sc.kisco;
-  for (int k = lane; k <= kend; k += 32) {
-    double S = sc.c0;
+  bool any = false;
+  for (int c = s; c * kChunkBins <= kend; c += kStreams) {
+    any = true;
+    const int kstop = min(kend, c * kChunkBins + kChunkBins - 1);
+    for (int k = c * kChunkBins + lane; k <= kstop; k += 32) {
+      double S = sc.c0;
 #pragma unroll
-    for (int j = 0; j < kNPn; ++j) S = fma(al[j], ev.b64[(int64_t)j * K + k], S);
-    const double f = ev.b64[(int64_t)8 * K + k];
-    double bf[kNBasis];
-    if (GRAD) {
-#pragma unroll
-      for (int j = 0; j < kNBasis; ++j) bf[j] = ev.b64[(int64_t)j * K + k];
-    }
-#pragma unroll
-    for (int a = 0; a < NDET; ++a) {
-      const double P = fma(f, sc.tau[a], S);
-      const double r = P - rint(P);
-      double sn, cs;
-      sincospi(2.0 * r, &sn, &cs);
-      const double2 E = ev.e64[(int64_t)a * K + k];
-      const double zr = E.x * cs + E.y * sn;
-      const double zi = E.y * cs - E.x * sn;
+      for (int j = 0; j < kNPn; ++j) S = fma(al[j], ev.b64[(int64_t)j * K + k], S);
+      const double f = ev.b64[(int64_t)8 * K + k];
+      double bf[kNBasis];
       if (GRAD) {
 #pragma unroll
-        for (int j = 0; j < kNBasis; ++j) {
-          acc[(a * kNMom + j) * 2] += zr * bf[j];
-          acc[(a * kNMom + j) * 2 + 1] += zi * bf[j];
+        for (int j = 0; j < kNBasis; ++j) bf[j] = ev.b64[(int64_t)j * K + k];
+      }
+#pragma unroll
+      for (int a = 0; a < NDET; ++a) {
+        const double P = fma(f, sc.tau[a], S);
+        const double r = P - rint(P);
+        double sn, cs;
+        sincospi(2.0 * r, &sn, &cs);
+        const double2 E = ev.e64[(int64_t)a * K + k];
+        const double zr = E.x * cs + E.y * sn;
+        const double zi = E.y * cs - E.x * sn;
+        if (GRAD) {
+#pragma unroll
+          for (int j = 0; j < kNBasis; ++j) {
+            acc[(a * kNMom + j) * 2] += zr * bf[j];
+            acc[(a * kNMom + j) * 2 + 1] += zi * bf[j];
+          }
+          acc[(a * kNMom + 9) * 2] += zr;
+          acc[(a * kNMom + 9) * 2 + 1] += zi;
+        } else {
+          acc[a * 2] += zr;
+          acc[a * 2 + 1] += zi;
         }
-        acc[(a * kNMom + 9) * 2] += zr;
-        acc[(a * kNMom + 9) * 2 + 1] += zi;
-      } else {
-        acc[a * 2] += zr;
-        acc[a * 2 + 1] += zi;
       }
     }
   }
-  // warp reduce-scatter (the same pairing as a butterfly sum per moment, with
-  // NP/2 + NP/4 + ... FP64 adds per lane instead of 5 NP)
   using F = FlushShape<NACC>;
   double v[F::NP];
 #pragma unroll
   for (int i = 0; i < F::NP; ++i) v[i] = i < NACC ? acc[i] : 0.0;
   ReduceScatter<F::NP, 16, double>::run(v, lane);
+#pragma unroll
+  for (int t = 0; t < F::KEEP; ++t) v_out[t] = v[t];
+  return any;
+}
+
+// FP64 moments of one particle on one warp; streams as in sweep_mixed (a
+// sweep below 2048 bins is its single stream).
+template <bool GRAD, int NDET>
+__device__ void sweep_fp64(const DevEvent& ev, const SweepCoef& sc, double* mom) {
+  constexpr int NACC = MomCount<NDET, GRAD>::value;
+  using F = FlushShape<NACC>;
+  const int lane = threadIdx.x & 31;
+  double v[F::KEEP], tot[F::KEEP];
+  if (sc.kisco < kChunkBins) {
+    fp64_stream<GRAD, NDET>(ev, sc, 0, tot);
+  } else {
+#pragma unroll
+    for (int t = 0; t < F::KEEP; ++t) tot[t] = 0.0;
+    for (int st = 0; st < kStreams; ++st) {
+      if (!fp64_stream<GRAD, NDET>(ev, sc, st, v)) break;
+#pragma unroll
+      for (int t = 0; t < F::KEEP; ++t) tot[t] += v[t];
+    }
+  }
   if (F::owner(lane)) {
 #pragma unroll
     for (int t = 0; t < F::KEEP; ++t) {
       const int idx = F::index(lane, t);
-      if (idx < NACC) mom[acc_to_mom<NDET, GRAD>(idx)] = v[t];
+      if (idx < NACC) mom[acc_to_mom<NDET, GRAD>(idx)] = tot[t];
     }
   }
 }

@@ -1,3 +1,7 @@
+// Autotuners. The standalone likelihood kernel's split factor (warps per
+// particle, sharing its bins by streams) is timed the same way on the
+// caller's own call; its results do not depend on the split either.
+//
 // Autotuner for the persistent NUTS launch: the slot count (particles per
 // CTA, i.e. the CTA's tile of particles) trades the FP64 cost of the per-
 // particle phases, which warp 0 runs with one lane per slot, against the
@@ -15,6 +19,9 @@ namespace sharpy {
 
 constexpr int kSlotChoices[] = {8, 16, 32};
 constexpr int kNumSlotChoices = 3;
+// Warps that share one particle's sweep in the standalone likelihood kernel.
+constexpr int kSplitChoices[] = {1, 2, 4, 8};
+constexpr int kNumSplitChoices = 4;
 
 struct TuneCandidate {
   int slots;

@@ -229,3 +229,33 @@ def test_autograd_backward_is_the_adjoint():
     (l * wts).sum().backward()
     _, g = ctx.loglike_grad(th.detach(), "mixed")
     assert torch.allclose(th.grad, g * wts[:, None], rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("wname", ["bbh11", "bns"])
+def test_loglike_split_factor_invariant(wname):
+    """The likelihood kernel cuts a vector's bins into chunks of 2048 dealt to 8 streams merged in a fixed
+    order, so the number of warps sharing a vector (1, 2, 4, 8: the tuner's choice) does not change ln L or
+    the gradient, bit for bit, on every path; on the 259585-bin segment the streams' merge stays within the
+    long-signal tolerance of the oracle. The tuner's pick is one of the candidates."""
+    G.require_gpu()
+    w = getattr(inputs, wname)()
+    ev, ctx, th_inj, _ = G.event_pair(w)
+    n = 40
+    th = np.vstack([inputs.prior_draws(w, n // 2, 6), inputs.ball(w, th_inj, n // 2, 7)])
+    t = G.to_dev(th)
+    for prec in ("fp64", "mixed", "split"):
+        ref = None
+        for split in (1, 2, 4, 8):
+            ctx.set_loglike_split(split)
+            l, g = ctx.loglike_grad(t, prec)
+            if ref is None:
+                ref = (l, g)
+            else:
+                assert torch.equal(l, ref[0]) and torch.equal(g, ref[1]), (prec, split)
+        if wname == "bns" and prec == "mixed":
+            lref = oracle.loglike(helpers.oracle_model(w), ev, th[:4], grad=False)
+            assert np.max(np.abs(ref[0].cpu().numpy()[:4] - lref)) <= 1e-2
+    ctx.set_loglike_split(0)
+    ctx.loglike_grad(t, "mixed")
+    assert ctx.loglike_split(n, "mixed") in (1, 2, 4, 8)
+    assert ctx.status() == 0

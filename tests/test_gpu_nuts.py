@@ -285,3 +285,30 @@ def test_mixed_state_machine_energy_error_against_fp64():
         spread = 3.0 * math.sqrt(np.var(a) / n + np.var(b) / n)
         assert abs(np.mean(a) - np.mean(b)) <= spread + 1e-3, (f, np.mean(a), np.mean(b), spread)
     assert ctx.status() == 0
+
+
+def test_nuts_long_signal_streams_match_oracle():
+    """The 259585-bin segment: its sweeps (~2e5 bins a detector) are cut into streams that the warps of a NUTS
+    tick share. FP64 path against the oracle's NUTS from the same 48 starts (same Philox counters), and the mixed
+    path's returned ln L against the standalone likelihood call at the returned theta (the same streams and
+    merge order: equal to rounding) and the FP64 value (long-signal tolerance)."""
+    G.require_gpu()
+    w = inputs.bns()
+    ev, ctx, th_inj, _ = G.event_pair(w)
+    model = helpers.oracle_model(w)
+    n = 48
+    th = inputs.ball(w, th_inj, n, 13, rel=1e-5)
+    t0 = G.to_dev(th)
+    l0, g0 = ctx.loglike_grad(t0, "fp64")
+    step = 0.5 * float(np.min(np.std(th, axis=0)))
+    ref = oracle.nuts_mutate(model, ev, 0.8, th, l0.cpu().numpy(), g0.cpu().numpy(), None, step, 3, 1, key=4, ctr=2)
+    t, l, g = t0.clone(), l0.clone(), g0.clone()
+    st = api.Context.stats_to_numpy(ctx.nuts_mutate(0.8, t, l, g, None, step, 3, 1, key=4, ctr=2, precision="fp64"))
+    _compare(t.cpu().numpy(), l.cpu().numpy(), st, ref[0], ref[1], ref[2], ref[3], G.width(w), frac=0.9)
+    t, l, g = t0.clone(), l0.clone(), g0.clone()
+    ctx.nuts_mutate(0.8, t, l, g, None, step, 3, 1, key=4, ctr=2, precision="mixed")
+    lm, _ = ctx.loglike_grad(t, "mixed")
+    l64, _ = ctx.loglike_grad(t, "fp64")
+    assert np.max(np.abs(lm.cpu().numpy() - l.cpu().numpy())) <= 1e-6 * max(1.0, float(l.abs().max()))
+    assert np.max(np.abs(l64.cpu().numpy() - l.cpu().numpy())) <= 1e-2
+    assert ctx.status() == 0
