@@ -36,17 +36,21 @@ UNIT = "evals/s"
 # Algorithmic work per active (bin, detector) of the gradient sweep with 3
 # detectors (FMA = 2 FLOP). Carrier and moments (all paths): angle scale 1,
 # complex multiply 6, moments 9 x 4 + 2 -> 45 FLOP (FP32 in the mixed paths).
-# mixed: FP64 phase, 8 FMA per bin shared by 3 detectors + 1 FMA per detector.
-# split: FP32 phase, 8 split products per bin (~13.5 FLOP each) shared by 3
-#        detectors + ~15 FLOP per detector -> 51 FLOP, total 96 FP32 FLOP.
-# fp64: phase as mixed, carrier by sincospi (~30 FMA) and moments in FP64.
+# mixed: the four large post-Newtonian terms as 4 FP64 FMA per bin shared by
+#        3 detectors, the four small ones as FP32 split products (~13.5 FLOP
+#        each) per bin, the delay term in FP32 per detector.
+# split: FP32 phase, 8 split products per bin shared by 3 detectors + ~15
+#        FLOP per detector -> 51 FLOP, total 96 FP32 FLOP.
+# fp64: all eight terms in FP64 FMA, carrier by sincospi (~30 FMA), moments in FP64.
+# These estimates stand in only while no instruction counts of the current
+# kernel sources are recorded (COUNTED below).
 def work(precision, n_det=3):
-    """Algorithmic FLOP per active (bin, detector) of the gradient sweep with n_det detectors."""
+    """Estimated FLOP per active (bin, detector) of the gradient sweep with n_det detectors."""
     poly64 = 2.0 * 8.0 / n_det                   # FP64 FMA: the 8-term PN polynomial, once per bin for all detectors
     delay32 = 15.0                               # FP32: f tau_a from hi/lo splits, per detector
     phase32 = 8.0 * 13.5 / n_det + delay32       # split FP32 phase: 8 split products per bin + the delay term
     if precision == "mixed":
-        return {"pipe": "fp64", "flop": poly64, "fp32_flop": delay32 + 45.0}
+        return {"pipe": "fp64", "flop": 2.0 * 4.0 / n_det, "fp32_flop": 4.0 * 13.5 / n_det + delay32 + 45.0}
     if precision == "split":
         return {"pipe": "fp32", "flop": phase32 + 45.0, "fp32_flop": phase32 + 45.0}
     return {"pipe": "fp64", "flop": poly64 + 2.0 + 60.0 + 45.0, "fp32_flop": 0.0}
@@ -55,23 +59,67 @@ def work(precision, n_det=3):
 WORK = {p: work(p) for p in ("mixed", "split", "fp64")}
 
 
-# DRAM bytes (read + write) of one NUTS launch of this workload from an ncu
-# capture of the bench's own launch, valid only for the kernel sources it was
-# taken on: reported as roofline.traffic while their hash matches.
-TRAFFIC_SOURCES = ["nuts_kernel.cuh", "sweep.cuh", "physics.cuh", "common.cuh"]
-TRAFFIC = {"sources_sha256_16": "d0074ef565d4152d",
-           "mixed": 3990016, "split": 3956480}
+# Counter-derived work and traffic, valid only for the kernel sources they
+# were taken on (reported while the sources' hash matches, else the estimates
+# above and traffic null). From one ncu launch each (`--mode nuts_launch
+# --ensemble late` for the NUTS kernel on the 11-D workload, `--mode
+# loglike_launch --workload bns --particles 1024` for the likelihood kernel):
+# FP64 FLOP = 2 DFMA + DADD + DMUL and FP32 FLOP = 2 FFMA + FADD + FMUL thread
+# instructions (smsp__sass_thread_inst_executed_op_*_pred_on.sum) per active
+# (bin, detector), and DRAM bytes read + written per launch.
+COUNTED_SOURCES = ["nuts_kernel.cuh", "sweep.cuh", "physics.cuh", "common.cuh", "dfloat.cuh", "loglike_kernel.cuh"]
+COUNTED = {"sources_sha256_16": "3f9075f39ee305da",
+           "nuts": {"mixed": {"fp64": 3.0888, "fp32": 106.99},
+                    "split": {"fp64": 0.3983, "fp32": 126.66},
+                    "fp64": {"fp64": 110.59, "fp32": 0.0152}},
+           "loglike": {},
+           "traffic": {"mixed": 3880448, "split": 3915008, "fp64": 4632064},
+           # the same captures: FP64 pipe busy, warps active and issue active
+           # (sm__inst_executed_pipe_fp64, sm__warps_active,
+           # smsp__issue_active; % of peak sustained active)
+           "util": {"mixed": {"fp64_pipe": 38.8, "warps_active": 10.7, "issue_active": 35.1},
+                    "split": {"fp64_pipe": 21.5, "warps_active": 10.7, "issue_active": 38.1},
+                    "fp64": {"fp64_pipe": 86.0, "warps_active": 11.0, "issue_active": 8.0}}}
+
+
+def _sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in COUNTED_SOURCES:
+        with open(os.path.join(ROOT, "paper_2601_02336_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def counted(kernel, precision):
+    """(fp64 FLOP, fp32 FLOP, source) per active (bin, detector) of `kernel` ('nuts' or 'loglike')."""
+    if COUNTED["sources_sha256_16"] == _sources_hash() and precision in COUNTED[kernel]:
+        c = COUNTED[kernel][precision]
+        return c["fp64"], c["fp32"], "ncu instruction counts of this kernel's sources"
+    wk = WORK[precision]
+    f64 = wk["flop"] if wk["pipe"] == "fp64" else 0.0
+    why = "sources changed since the counts" if COUNTED["sources_sha256_16"] != _sources_hash() else "no counts recorded"
+    return f64, wk["fp32_flop"] if wk["pipe"] == "fp64" else wk["flop"], f"hand estimate ({why})"
 
 
 def _traffic(precision):
-    import hashlib
-    h = hashlib.sha256()
-    for f in TRAFFIC_SOURCES:
-        with open(os.path.join(ROOT, "paper_2601_02336_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    if h.hexdigest()[:16] != TRAFFIC["sources_sha256_16"]:
+    if COUNTED["sources_sha256_16"] != _sources_hash():
         return None
-    return TRAFFIC.get(precision)
+    return COUNTED["traffic"].get(precision)
+
+
+def _util(precision):
+    if COUNTED["sources_sha256_16"] != _sources_hash():
+        return None
+    return COUNTED["util"].get(precision)
+
+
+def binding_pipe(f64, f32, p64, p32):
+    """(pipe, FLOP per unit, peak) of the pipe that bounds a kernel doing f64 FP64 and f32 FP32 FLOP per unit:
+    the one whose work takes longer at its peak (the two pipes issue concurrently)."""
+    if p32 and f32 / p32 > f64 / p64:
+        return "fp32", f32, p32
+    return "fp64", f64, p64
 
 
 def _env_int(k, d):
@@ -248,11 +296,13 @@ def main_loglike(args):
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
-            wk = work(prec, w.n_det)
-            tfl = n * act * wk["flop"] / (ms * 1e-3) / 1e12
-            peak = peaks[1] if wk["pipe"] == "fp64" else peaks[0]
-            row[prec] = {"evals_per_s": n / (ms * 1e-3), "ms_per_call": ms, "pipe": wk["pipe"],
-                         "achieved_tflops": tfl, "frac": tfl / peak}
+            f64c, f32c, fsrc = counted("loglike", prec)
+            pipe, flop, peak = binding_pipe(f64c, f32c, peaks[1], peaks[0])
+            tfl = n * act * flop / (ms * 1e-3) / 1e12
+            row[prec] = {"evals_per_s": n / (ms * 1e-3), "ms_per_call": ms, "pipe": pipe,
+                         "flop_per_active_bin_det": flop, "flop_source": fsrc,
+                         "achieved_tflops": tfl, "frac": tfl / peak,
+                         "warps_per_vector_tuned": ctx.loglike_split(n, prec)}
         out["sets"][name] = row
     # oracle on 64 vectors of the ball set, and the mixed path's error against it
     oracle.build()
@@ -317,9 +367,10 @@ def _extra_workloads(args, flush):
                        "prior width), one sharpy_loglike_grad call = ln L + gradient of all 8192",
            "active_bin_det_per_eval": float(_active_bins(w, th.cpu().numpy()).mean())}
     for prec in ("mixed", "fp64"):
-        ctx.loglike_grad(th, prec)
+        ctx.loglike_grad(th, prec)  # the first call of this shape tunes the warps per vector
         _, ms = timed(lambda: ctx.loglike_grad(th, prec))
-        row[prec] = {"ms_per_call": ms, "evals_per_s": 8192 / (ms * 1e-3)}
+        row[prec] = {"ms_per_call": ms, "evals_per_s": 8192 / (ms * 1e-3),
+                     "warps_per_vector_tuned": ctx.loglike_split(8192, prec)}
     out["bns_loglike_grad"] = row
     del ctx, th
     ws = inputs.batch64()
@@ -466,7 +517,8 @@ def main_batch(args):
     total = multirank.reduce_scalar(evals, "sum", world, device="cuda")
     n_ev = len(ws) * args.steps * world
     if rank == 0:
-        wk = WORK[args.precision]
+        f64c, f32c, _ = counted("nuts", args.precision)
+        wk = {"flop": f32c if args.precision == "split" else f64c}  # the pipe that binds on the 11-D workload
         out = {"metric": METRIC, "value": total / (t_max * 1e-3), "unit": UNIT, "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -599,20 +651,23 @@ def main():
     peaks = (C.c_double * 3)()
     lib().sharpy_probe_peaks(local, peaks)
     fp32_peak, fp64_peak = peaks[0], peaks[1]
-    wk = work(args.precision, w.n_det)
+    f64c, f32c, fsrc = counted("nuts", args.precision)
+    pipe, flop, peak = binding_pipe(f64c, f32c, fp64_peak, fp32_peak)
     secs = nuts_ms * 1e-3
-    ach = bins * wk["flop"] / secs / 1e12
-    peak = fp64_peak if wk["pipe"] == "fp64" else fp32_peak
-    fp32_ach = bins * wk["fp32_flop"] / secs / 1e12
+    ach = bins * flop / secs / 1e12
+    fp64_ach, fp32_ach = bins * f64c / secs / 1e12, bins * f32c / secs / 1e12
     kname = {"mixed": "MIXED", "split": "MIXED_SPLIT", "fp64": "FP64"}[args.precision]
     roofline = {"bound": "alu", "kernel": f"nuts_kernel<{kname},{w.n_det}>", "achieved": ach, "peak": peak,
                 "unit": "TFLOP/s", "frac": ach / peak if peak else None,
                 "traffic": _traffic(args.precision) if w.name == "bbh11" else None,
                 "traffic_unit": "bytes per NUTS launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-                "pipe": wk["pipe"], "flop_per_active_bin_det": wk["flop"],
-                "peak_source": f"measured {wk['pipe'].upper()} FMA probe on this GPU (sharpy_probe_peaks)",
+                "pipe": pipe, "flop_per_active_bin_det": flop, "flop_source": fsrc,
+                "fp64_flop_per_active_bin_det": f64c, "fp32_flop_per_active_bin_det": f32c,
+                "peak_source": f"measured {pipe.upper()} FMA probe on this GPU (sharpy_probe_peaks)",
+                "fp64_achieved": fp64_ach, "fp64_frac": fp64_ach / fp64_peak if fp64_peak else None,
                 "fp32_achieved": fp32_ach, "fp32_peak": fp32_peak,
                 "fp32_frac": fp32_ach / fp32_peak if fp32_peak else None, "fp64_peak": fp64_peak,
+                "ncu_pipe_utilisation_pct": _util(args.precision) if w.name == "bbh11" else None,
                 "nuts_share_of_step": nuts_ms / t_rank,
                 "reweight_share_of_step": rew_ms / t_rank,
                 "active_bin_det_per_eval": bins / max(evals, 1)}
