@@ -424,7 +424,10 @@ def main_nuts_launch(args):
             if k >= args.warmup:
                 times.append(e0.elapsed_time(e1))
                 st = api.Context.stats_to_numpy(s)
+        import hashlib
+        digest = hashlib.sha256(b"".join(a.cpu().numpy().tobytes() for a in (t, l, g))).hexdigest()[:16]
         out["ensembles"][name] = {"beta": beta, "step": eps, "ms_median": float(np.median(times)),
+                                  "state_sha256_16": digest,
                                   "ms_min": float(np.min(times)), "launches": len(times),
                                   "active_bin_det": float(st["active_bins"].sum()),
                                   "n_leapfrog": int(st["n_leapfrog"].sum()),

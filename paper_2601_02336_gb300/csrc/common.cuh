@@ -22,6 +22,11 @@ constexpr int kMaxDim = SHARPY_MAX_DIM;
 constexpr int kMaxDet = SHARPY_MAX_DET;
 constexpr int kNBasis = 9;  // x^5, x^3, x^2, x, ln f, y, y ln f, y^2, f  (x = f^-1/3, y = f^1/3)
 constexpr int kNPn = 8;     // the first eight: post-Newtonian phase basis
+// The mixed sweep's split of the post-Newtonian basis: terms accumulated in
+// FP64 (x^5, x^3, x^2, ln f) and terms formed in FP32 pairs (x, y, y ln f, y^2).
+__host__ __device__ constexpr int large_pn(int i) { return i < 3 ? i : 4; }
+__host__ __device__ constexpr int small_pn(int i) { return i == 0 ? 3 : i + 4; }
+__host__ __device__ constexpr bool is_large_pn(int j) { return j < 3 || j == 4; }
 
 // Model configuration as passed to kernels (by value).
 struct DevModel {
@@ -55,6 +60,7 @@ struct DevEvent {
   double f_min, df;
   double inv_df;             // 1 / df (k_ISCO guess; the table decides)
   double dd;                 // <d|d> over all bins and detectors
+  float ddh_hi, ddh_lo;      // -<d|d>/2 as a double-float: hi = (float)x, lo = (float)(x - hi)
   const double* f;           // [K] f_k
   const double* b64;         // [kNBasis][K] basis functions (FP64)
   const float* b32;          // [kNBasis][K] basis functions (FP32, = hi part)

@@ -264,6 +264,11 @@ int sharpy_set_data(sharpy_ctx* c, int n_det, int64_t n_bins, double f_min, doub
   ev.df = df;
   ev.inv_df = 1.0 / df;
   ev.dd = dd + ddc;
+  {
+    const double h = -0.5 * ev.dd;  // the epilogue's starting sum, as a double-float
+    ev.ddh_hi = (float)h;
+    ev.ddh_lo = (float)(h - (double)ev.ddh_hi);
+  }
   ev.f = c->d_f;
   ev.b64 = c->d_b64;
   ev.b32 = c->d_b32;

@@ -118,7 +118,8 @@ struct Slot {
   int n_leaf, divergent;
   int done;
   // stats
-  double st_acc, st_bins;
+  double st_acc;
+  long long st_bins;  // active (bin, detector) pairs, summed exactly in integers
   int st_depth, st_leap, st_div;
 };
 
@@ -134,6 +135,7 @@ struct NutsShared {
   int mstride;
   long long lokey[kMaxDim], hikey[kMaxDim];  // order keys of the prior box (see okey)
   double eps, beta;
+  VT epsv;          // eps in the state machine's type
   double lp_const;  // sum of the prior's constant log terms
   int metric_kind;
   int alive;
@@ -291,9 +293,11 @@ struct Nuts {
   }
 
   // Boundary maps on the pending leaf (P_N, F_NR). False if not finite.
-  // Periodic dimensions wrap lane-parallel (no momentum change); reflections,
-  // whose momentum update reads the whole velocity, run dimension by
-  // dimension in order (rare: a leaf outside the box).
+  // Periodic dimensions wrap lane-parallel (no momentum change). Reflections
+  // also run lane-parallel with an identity or diagonal metric, where a
+  // reflection changes only its own dimension's momentum; with a dense metric
+  // the momentum update reads the whole velocity, so they run dimension by
+  // dimension in order.
   __device__ bool boundary() {
     const DevModel& m = A.m;
     bool ok = true, reflect = false;
@@ -307,11 +311,14 @@ struct Nuts {
         ok = false;
         continue;
       }
+      const long long q = okey(x);
       if (m.boundary[d] != SHARPY_BOUND_PERIODIC) {
-        const long long q = okey(x);
         if (q < S.lokey[d] || q > S.hikey[d]) reflect = true;
         continue;
       }
+      // lo = +0 and +0 <= x < hi: the wrap below returns x itself (x - 0 = x,
+      // 0 + x = x); skip its FP64 arithmetic
+      if (S.lokey[d] == 0 && q >= 0 && q < S.hikey[d]) continue;
       // lo + ((x - lo) mod w): for |x - lo| < 2w one exact subtraction or
       // addition gives fmod's result; fmod only for larger excursions
       const double lo = m.lo[d], w = m.hi[d] - lo;
@@ -325,6 +332,33 @@ struct Nuts {
     }
     if (!__all_sync(gm, ok)) return false;
     if (!__any_sync(gm, reflect)) return true;
+    if (S.metric_kind != METRIC_DENSE) {
+      bool bad = false;
+#pragma unroll
+      for (int k = 0; k < DPL; ++k) {
+        const int d = dim(k);
+        if (!has(k) || m.boundary[d] == SHARPY_BOUND_PERIODIC) continue;
+        const double lo = m.lo[d], hi = m.hi[d];
+        double x = X(P_N, d);
+        int flips = 0;
+        while ((x < lo || x > hi) && flips < 100) {
+          x = x < lo ? 2.0 * lo - x : 2.0 * hi - x;
+          ++flips;
+        }
+        if (x < lo || x > hi) {
+          bad = true;  // the leaf is discarded as divergent: nothing written matters
+          continue;
+        }
+        X(P_N, d) = x;
+        if (flips & 1) {
+          const VT vi = S.metric_kind == METRIC_IDENTITY ? V(F_NR, d) : MI(d, d) * V(F_NR, d);
+          V(F_NR, d) = V(F_NR, d) - VT(2) * vi / MI(d, d);
+        }
+      }
+      if (__any_sync(gm, bad)) return false;
+      sync();
+      return true;
+    }
     for (int i = 0; i < D; ++i) {
       if (m.boundary[i] == SHARPY_BOUND_PERIODIC) continue;
       const double lo = m.lo[i], hi = m.hi[i];
@@ -363,16 +397,17 @@ struct Nuts {
   // First half of a leapfrog from the end of the tree in direction dir.
   __device__ bool begin_leapfrog(int dir) {
     const int pth = dir > 0 ? P_R : P_L, fr = dir > 0 ? F_RR : F_LR, fgu = dir > 0 ? F_RGU : F_LGU;
-    const double h = dir * S.eps;
-    const VT hv = (VT)h;
+    const VT hv = dir > 0 ? S.epsv : -S.epsv;  // = (VT)(dir * eps)
 #pragma unroll
     for (int k = 0; k < DPL; ++k)
       if (has(k)) V(F_NR, dim(k)) = V(fr, dim(k)) - VT(0.5) * hv * V(fgu, dim(k));
     VT v[DPL];
     velocity(F_NR, v);
+    // x + (dir eps) v as x + eps (dir v): the same exact product, so the same
+    // rounding, without forming -eps in FP64
 #pragma unroll
     for (int k = 0; k < DPL; ++k)
-      if (has(k)) X(P_N, dim(k)) = X(pth, dim(k)) + h * (double)v[k];
+      if (has(k)) X(P_N, dim(k)) = X(pth, dim(k)) + S.eps * (double)(dir > 0 ? v[k] : -v[k]);
     return boundary();
   }
 
@@ -463,7 +498,7 @@ struct Nuts {
   __device__ bool advance(Slot<VT>& sl, bool have_leaf, const VT* gl_new, double lp_new, const VT* glp_new) {
     if (have_leaf) {
       // complete the leapfrog
-      const VT h = (VT)(sl.dir * S.eps);
+      const VT h = sl.dir > 0 ? S.epsv : -S.epsv;  // = (VT)(dir * eps)
       const VT bv = (VT)S.beta;
       VT gu[DPL];
 #pragma unroll
@@ -720,6 +755,7 @@ __global__ void __launch_bounds__(kNutsWarps * 32, PREC == SHARPY_FP64 ? 2 : 3)
       eps = A.step * smin;
     }
     S.eps = eps;
+    S.epsv = (VT)eps;
     S.beta = A.beta_ptr ? *A.beta_ptr : A.beta;
   }
   __syncthreads();
@@ -740,7 +776,8 @@ __global__ void __launch_bounds__(kNutsWarps * 32, PREC == SHARPY_FP64 ? 2 : 3)
     sl.pid = (int64_t)s_block * SLOTS + my;
     sl.t = 0;
     sl.done = 1;
-    sl.st_acc = sl.st_bins = 0.0;
+    sl.st_acc = 0.0;
+    sl.st_bins = 0;
     sl.st_depth = sl.st_leap = sl.st_div = 0;
     bool active = false;
     if (sl.pid < A.n) {
@@ -910,7 +947,7 @@ __global__ void __launch_bounds__(kNutsWarps * 32, PREC == SHARPY_FP64 ? 2 : 3)
         sl.lnl_new = NAN;
         if (sc[cs].ok) {
           epilogue<DT, true>(A.ev, sc[cs], ec[cs], mom[cs], &sl.lnl_new, gph);
-          sl.st_bins += (double)(sc[cs].kisco + 1) * A.ev.n_det;
+          sl.st_bins += (long long)(sc[cs].kisco + 1) * A.ev.n_det;
         }
 #pragma unroll
         for (int k = 0; k < DPL; ++k)
@@ -952,7 +989,7 @@ __global__ void __launch_bounds__(kNutsWarps * 32, PREC == SHARPY_FP64 ? 2 : 3)
     if (A.stats) {
       sharpy_nuts_stats st;
       st.accept_sum = sl.st_acc;
-      st.active_bins = sl.st_bins;
+      st.active_bins = (double)sl.st_bins;
       st.depth_sum = sl.st_depth;
       st.n_leapfrog = sl.st_leap;
       st.n_divergent = sl.st_div;

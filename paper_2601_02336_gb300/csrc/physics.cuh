@@ -181,6 +181,8 @@ __device__ __forceinline__ void split2(double x, float* hi, float* lo) {
 template <class DT>
 struct EpiCoef {
   double A0;
+  double A0sq;                            // A0 * A0
+  DT a0;                                  // A0 in the epilogue's type
   DT cre[kMaxDet], cim[kMaxDet];          // C_a
   DT dalpha[kNPn][4];                     // d alpha_j / d(Mc, q, chi1, chi2)
   DT dc0[4];
@@ -377,9 +379,19 @@ __device__ __forceinline__ int isco_bin(const DevEvent& ev, double fisco) {
 }
 
 // Whether theta lies in the model's domain (both halves of the prologue test it).
+// x > 0 and |x| <= 1 decided on the bits of x (integer pipes, not the FP64
+// one), with the comparisons' own results for every input: NaN fails both,
+// +inf passes the first.
+__device__ __forceinline__ bool bits_positive(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && b <= 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool bits_abs_le1(double x) {
+  return (__double_as_longlong(x) & 0x7fffffffffffffffLL) <= 0x3ff0000000000000LL;
+}
 __device__ __forceinline__ bool phys_ok(const double* ph) {
-  return ph[SHARPY_MC] > 0.0 && ph[SHARPY_Q] > 0.0 && ph[SHARPY_DL] > 0.0 && fabs(ph[SHARPY_SINDEC]) <= 1.0 &&
-         fabs(ph[SHARPY_COSI]) <= 1.0;
+  return bits_positive(ph[SHARPY_MC]) && bits_positive(ph[SHARPY_Q]) && bits_positive(ph[SHARPY_DL]) &&
+         bits_abs_le1(ph[SHARPY_SINDEC]) && bits_abs_le1(ph[SHARPY_COSI]);
 }
 
 // The prologue in two independent halves, so that two warps can run them at
@@ -400,9 +412,12 @@ __device__ void prologue_phase(const DevModel& m, const DevEvent& ev, const doub
   I4<DT> alpha[kNPn], cpn;
   double mtot, fisco;
   pn_coefficients<DT>(ph, alpha, cpn, mtot, fisco);
+  // the mixed sweep reads the four large terms' coefficients in FP64 and the
+  // others as FP32 pairs: only the four get an FP64 copy there
+  constexpr bool kAllF64 = SPLIT || std::is_same<DT, double>::value;
 #pragma unroll
   for (int j = 0; j < kNPn; ++j) {
-    sc.alpha[j] = vdbl(alpha[j].v);
+    if (kAllF64 || is_large_pn(j)) sc.alpha[j] = vdbl(alpha[j].v);
     if (GRAD)
 #pragma unroll
       for (int i = 0; i < 4; ++i) ec.dalpha[j][i] = alpha[j].d[i];
@@ -450,6 +465,8 @@ __device__ void prologue_sky(const DevModel& m, const DevEvent& ev, const double
     const DF Y1 = Y + Y * ((1.0 / 6.0) * t);
     ec.A0 = df_to_double((kAmp * Y1) * df_recip(df_from(ph[SHARPY_DL] * kMpcSec)));
   }
+  ec.A0sq = ec.A0 * ec.A0;
+  ec.a0 = (DT)ec.A0;
   if (GRAD) {
     ec.rel_mc = DT(5.0 / 6.0) / mc;
     ec.rel_dl = DT(-1) / dl;
@@ -513,16 +530,16 @@ __device__ void epilogue(const DevEvent& ev, const SweepCoef& sc, const EpiCoef<
                          GT* gph) {
   constexpr bool kDF = std::is_same<DT, float>::value;
   double acc = -0.5 * ev.dd;
-  DF accf = kDF ? df_from(acc) : DF{0.0f, 0.0f};
+  DF accf = kDF ? DF{ev.ddh_hi, ev.ddh_lo} : DF{0.0f, 0.0f};  // = df_from(acc), formed when the data were set
   DT g[SHARPY_NPHYS];
 #pragma unroll
   for (int i = 0; i < SHARPY_NPHYS; ++i) g[i] = DT(0);
-  const DT a0 = (DT)ec.A0;
+  const DT a0 = ec.a0;
   for (int a = 0; a < ev.n_det; ++a) {
     const MT* M = mom + a * kNMom * 2;
     const double P = sc.kisco >= 0 ? ev.pref[(int64_t)a * ev.n_bins + sc.kisco] : 0.0;
     const DT cr = ec.cre[a], ci = ec.cim[a];
-    const DT ps = (DT)(ec.A0 * ec.A0 * P);             // A0^2 P
+    const DT ps = (DT)(ec.A0sq * P);                   // A0^2 P
     const DT zr = a0 * (DT)M[18], zi = a0 * (DT)M[19];  // A0 Z
     if constexpr (kDF) {
       // Re(C A0 Z) - |C|^2 A0^2 P / 2

@@ -36,10 +36,6 @@ constexpr int kFlush = 64;  // lane iterations per FP32 block
 // order, so any number of warps per particle gives the same moments.
 constexpr int kChunkBins = kFlush * 32;
 constexpr int kStreams = 8;
-// The mixed sweep's split of the post-Newtonian basis: terms accumulated in
-// FP64 (x^5, x^3, x^2, ln f) and terms formed in FP32 pairs (x, y, y ln f, y^2).
-__host__ __device__ constexpr int large_pn(int i) { return i < 3 ? i : 4; }
-__host__ __device__ constexpr int small_pn(int i) { return i == 0 ? 3 : i + 4; }
 
 template <int NDET, bool GRAD>
 struct MomCount {
