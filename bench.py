@@ -68,17 +68,17 @@ WORK = {p: work(p) for p in ("mixed", "split", "fp64")}
 # instructions (smsp__sass_thread_inst_executed_op_*_pred_on.sum) per active
 # (bin, detector), and DRAM bytes read + written per launch.
 COUNTED_SOURCES = ["nuts_kernel.cuh", "sweep.cuh", "physics.cuh", "common.cuh", "dfloat.cuh", "loglike_kernel.cuh"]
-COUNTED = {"sources_sha256_16": "3f9075f39ee305da",
-           "nuts": {"mixed": {"fp64": 3.0888, "fp32": 106.99},
-                    "split": {"fp64": 0.3983, "fp32": 126.66},
-                    "fp64": {"fp64": 110.59, "fp32": 0.0152}},
+COUNTED = {"sources_sha256_16": "4fc80ab8d879d02e",
+           "nuts": {"mixed": {"fp64": 2.9620, "fp32": 107.01},
+                    "split": {"fp64": 0.2756, "fp32": 126.67},
+                    "fp64": {"fp64": 110.50, "fp32": 0.0152}},
            "loglike": {},
-           "traffic": {"mixed": 3880448, "split": 3915008, "fp64": 4632064},
+           "traffic": {"mixed": 3839232, "split": 3805440, "fp64": 4508160},
            # the same captures: FP64 pipe busy, warps active and issue active
            # (sm__inst_executed_pipe_fp64, sm__warps_active,
            # smsp__issue_active; % of peak sustained active)
-           "util": {"mixed": {"fp64_pipe": 38.8, "warps_active": 10.7, "issue_active": 35.1},
-                    "split": {"fp64_pipe": 21.5, "warps_active": 10.7, "issue_active": 38.1},
+           "util": {"mixed": {"fp64_pipe": 34.3, "warps_active": 10.7, "issue_active": 36.8},
+                    "split": {"fp64_pipe": 16.8, "warps_active": 10.7, "issue_active": 40.5},
                     "fp64": {"fp64_pipe": 86.0, "warps_active": 11.0, "issue_active": 8.0}}}
 
 
