@@ -72,7 +72,10 @@ COUNTED = {"sources_sha256_16": "4fc80ab8d879d02e",
            "nuts": {"mixed": {"fp64": 2.9620, "fp32": 107.01},
                     "split": {"fp64": 0.2756, "fp32": 126.67},
                     "fp64": {"fp64": 110.50, "fp32": 0.0152}},
-           "loglike": {},
+           # the likelihood kernel: one call on 1024 vectors near the injection of
+           # the 259585-bin segment (the tuned 8 / 4 warps per vector)
+           "loglike": {"mixed": {"fp64": 2.6689, "fp32": 81.405},
+                       "fp64": {"fp64": 90.365, "fp32": 0.0}},
            "traffic": {"mixed": 3839232, "split": 3805440, "fp64": 4508160},
            # the same captures: FP64 pipe busy, warps active and issue active
            # (sm__inst_executed_pipe_fp64, sm__warps_active,
