@@ -174,18 +174,24 @@ int sharpy_prior_logpdf_grad(sharpy_ctx* ctx, int64_t n, const double* theta, do
    grad [N][D] or NULL (forward-only sweep): device arrays. precision:
    SHARPY_FP64 / SHARPY_MIXED / SHARPY_MIXED_SPLIT. The bins of one vector
    are cut into chunks of 2048 dealt to 8 streams that are merged in a fixed
-   order, and 1, 2, 4 or 8 warps share a vector's streams: the first call for
-   a (bins, detectors, N, precision, gradient) shape times the four choices
-   on its own arguments (synchronising `stream`; the outputs do not depend on
+   order, and 1, 2, 4 or 8 warps share a vector's streams. On segments of
+   65536 bins or more, SHARPY_MIXED has a fifth choice (16): one vector per
+   warp, eight vectors per CTA reading each block of 256 bins' tables from
+   shared memory, where one bulk copy brings it (sharpy_set_data lays the
+   tables out in such blocks, 28 KB each for three detectors). The first call
+   for a (bins, detectors, N, precision, gradient) shape times the choices on
+   its own arguments (synchronising `stream`; the outputs do not depend on
    the choice) and the context keeps the fastest; later calls are
-   asynchronous. */
+   asynchronous. A bulk copy that does not complete within its wait bound
+   sets SHARPY_ETIMEOUT in the status word. */
 int sharpy_loglike_grad(sharpy_ctx* ctx, int64_t n, const double* theta, double* lnl, double* grad,
                         int precision, sharpy_stream stream);
 /* The warps per vector the context picked for sharpy_loglike_grad calls of
    N vectors at `precision` (with_grad: with or without the gradient) on its
    current event's grid; 0 before the first such call. */
 int sharpy_loglike_split(sharpy_ctx* ctx, int64_t n, int precision, int with_grad);
-/* Use `split` (1, 2, 4 or 8) warps per vector in every later
+/* Use `split` (1, 2, 4 or 8 warps per vector, or 16: the staged kernel,
+   which falls back to 8 where it does not apply) in every later
    sharpy_loglike_grad call of the context instead of the tuned choice; 0
    returns to tuning. SHARPY_EINVAL for other values. */
 int sharpy_set_loglike_split(sharpy_ctx* ctx, int split);

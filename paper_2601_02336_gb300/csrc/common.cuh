@@ -28,6 +28,28 @@ __host__ __device__ constexpr int large_pn(int i) { return i < 3 ? i : 4; }
 __host__ __device__ constexpr int small_pn(int i) { return i == 0 ? 3 : i + 4; }
 __host__ __device__ constexpr bool is_large_pn(int j) { return j < 3 || j == 4; }
 
+// Staged tables of a long segment (K >= kStageMinBins): one contiguous record
+// per block of kStageBins bins, so that one bulk copy brings a block's tables
+// into shared memory. Record layout (bins g kStageBins + i, i < kStageBins;
+// zeros past the last bin):
+//   float  b32[9][kStageBins]       basis functions, FP32 hi parts
+//   float  lo[5][kStageBins]        FP32 lo parts of x, y, y ln f, y^2 and f
+//   double b64[4][kStageBins]       x^5, x^3, x^2, ln f in FP64
+//   float2 e32[n_det][kStageBins]   pre-whitened data
+// Every offset and the record size are multiples of 16 bytes.
+constexpr int kStageBins = 256;
+constexpr int64_t kStageMinBins = 65536;
+__host__ __device__ constexpr int stage_off_lo() { return kNBasis * kStageBins * 4; }
+__host__ __device__ constexpr int stage_off_b64() { return stage_off_lo() + 5 * kStageBins * 4; }
+__host__ __device__ constexpr int stage_off_e32() { return stage_off_b64() + 4 * kStageBins * 8; }
+__host__ __device__ constexpr int stage_rec_bytes(int n_det) { return stage_off_e32() + n_det * kStageBins * 8; }
+// row of basis function j among the staged lo parts (j = 3, 5, 6, 7, 8) and FP64 rows (j = 0, 1, 2, 4)
+__host__ __device__ constexpr int stage_lo_row(int j) { return j == 3 ? 0 : j == 5 ? 1 : j == 6 ? 2 : j == 7 ? 3 : 4; }
+__host__ __device__ constexpr int stage_b64_row(int j) { return j == 4 ? 3 : j; }
+static_assert(stage_off_lo() % 16 == 0 && stage_off_b64() % 16 == 0 && stage_off_e32() % 16 == 0 &&
+                  stage_rec_bytes(1) % 16 == 0,
+              "bulk copies move multiples of 16 bytes between 16-byte aligned addresses");
+
 // Model configuration as passed to kernels (by value).
 struct DevModel {
   int model;
@@ -70,6 +92,8 @@ struct DevEvent {
   const double* pref;        // [n_det][K] prefix sums of w f^-7/3
   const double* p1;          // [n_det][kNBasis][K] prefix sums of w f^-7/3 B_m (Fisher), or null
   const double* p2;          // [n_det][kNBasis (kNBasis + 1) / 2][K] ... B_m B_n, m <= n, or null
+  const unsigned char* stage;  // staged records (see stage_rec_bytes), or null for K < kStageMinBins
+  int stage_blocks;            // records: ceil(K / kStageBins)
   DevDetector det[kMaxDet];
 };
 

@@ -29,6 +29,25 @@ int check_ctx(sharpy_ctx* ctx, bool need_data) {
   return SHARPY_OK;
 }
 
+// One CTA per staged record: thread i copies bin g kStageBins + i of every
+// table the mixed sweep reads (zeros past the last bin).
+__global__ void stage_tables_kernel(DevEvent ev, unsigned char* out) {
+  const int g = blockIdx.x, i = threadIdx.x;
+  const int64_t K = ev.n_bins, k = (int64_t)g * kStageBins + i;
+  const bool in = k < K;
+  unsigned char* rec = out + (size_t)g * stage_rec_bytes(ev.n_det);
+  float* b32 = reinterpret_cast<float*>(rec);
+  float* lo = reinterpret_cast<float*>(rec + stage_off_lo());
+  double* b64 = reinterpret_cast<double*>(rec + stage_off_b64());
+  float2* e32 = reinterpret_cast<float2*>(rec + stage_off_e32());
+  for (int j = 0; j < kNBasis; ++j) b32[j * kStageBins + i] = in ? ev.b32[j * K + k] : 0.0f;
+  constexpr int lo_j[5] = {3, 5, 6, 7, 8};
+  for (int r = 0; r < 5; ++r) lo[r * kStageBins + i] = in ? ev.b32lo[lo_j[r] * K + k] : 0.0f;
+  constexpr int b64_j[4] = {0, 1, 2, 4};
+  for (int r = 0; r < 4; ++r) b64[r * kStageBins + i] = in ? ev.b64[b64_j[r] * K + k] : 0.0;
+  for (int a = 0; a < ev.n_det; ++a) e32[a * kStageBins + i] = in ? ev.e32[a * K + k] : make_float2(0.0f, 0.0f);
+}
+
 }  // namespace sharpy
 
 static void free_event(sharpy_ctx* c) {
@@ -41,6 +60,10 @@ static void free_event(sharpy_ctx* c) {
   cudaFree(c->d_pref);
   cudaFree(c->d_p1);
   cudaFree(c->d_p2);
+  cudaFree(c->d_stage);
+  c->d_stage = nullptr;
+  c->ev.stage = nullptr;
+  c->ev.stage_blocks = 0;
   c->d_p1 = c->d_p2 = nullptr;
   c->ev.p1 = c->ev.p2 = nullptr;
   c->d_f = c->d_b64 = c->d_pref = nullptr;
@@ -279,6 +302,25 @@ int sharpy_set_data(sharpy_ctx* c, int n_det, int64_t n_bins, double f_min, doub
   ev.p1 = c->d_p1;
   ev.p2 = c->d_p2;
   for (int a = 0; a < n_det; ++a) detector_geometry(det[a], ev.det[a]);
+  // staged records of a long segment (rebuilt with every data set: they hold E)
+  if (c->model.model == SHARPY_MODEL_TAYLORF2 && K >= kStageMinBins) {
+    const int nb = (int)((K + kStageBins - 1) / kStageBins);
+    if (!c->d_stage && cudaMalloc(&c->d_stage, (size_t)nb * stage_rec_bytes(n_det)) != cudaSuccess) {
+      c->d_stage = nullptr;
+      free_event(c);
+      return SHARPY_ENOMEM;
+    }
+    stage_tables_kernel<<<nb, kStageBins>>>(ev, c->d_stage);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+      free_event(c);
+      return SHARPY_ECUDA;
+    }
+    ev.stage = c->d_stage;
+    ev.stage_blocks = nb;
+  } else {
+    ev.stage = nullptr;
+    ev.stage_blocks = 0;
+  }
   c->has_data = true;
   return SHARPY_OK;
 }

@@ -33,6 +33,7 @@ struct sharpy_ctx {
   float* d_b32lo = nullptr;
   double2* d_e64 = nullptr;
   float2* d_e32 = nullptr;
+  unsigned char* d_stage = nullptr;  // staged records of a long segment
   double* d_pref = nullptr;
   // status word and evidence accumulator (device)
   int* d_status = nullptr;

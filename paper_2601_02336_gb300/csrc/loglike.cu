@@ -107,13 +107,16 @@ static int launch_ll(sharpy_ctx* c, int64_t n, const double* th, double* lnl, do
   for (const auto& e : c->ll_tuned)
     if (e.key == key) return launch_ll_prec<PREC, GRAD>(c, e.split, n, th, lnl, grad, s) == cudaSuccess
                                  ? SHARPY_OK : SHARPY_ECUDA;
-  TuneCandidate cands[kNumSplitChoices];
-  for (int i = 0; i < kNumSplitChoices; ++i) cands[i].slots = kSplitChoices[i];
+  // 1, 2, 4, 8 warps per vector, and the staged kernel where it applies
+  TuneCandidate cands[kNumSplitChoices + 1];
+  int nc = 0;
+  for (int i = 0; i < kNumSplitChoices; ++i) cands[nc++].slots = kSplitChoices[i];
+  if (PREC == SHARPY_MIXED && c->ev.stage) cands[nc++].slots = kSplitStaged;
   auto trial = [&](int split, cudaStream_t ts) -> int {
     return launch_ll_prec<PREC, GRAD>(c, split, n, th, lnl, grad, ts) == cudaSuccess ? SHARPY_OK : SHARPY_ECUDA;
   };
   int best = 1;
-  const int rc = tune_slots(cands, kNumSplitChoices, trial, s, &best);
+  const int rc = tune_slots(cands, nc, trial, s, &best);
   if (rc) return rc;
   c->ll_tuned.push_back({key, best});
   return SHARPY_OK;
@@ -153,7 +156,8 @@ int sharpy_loglike_grad(sharpy_ctx* c, int64_t n, const double* theta, double* l
 int sharpy_set_loglike_split(sharpy_ctx* c, int split) {
   int rc = check_ctx(c, false);
   if (rc) return rc;
-  if (split != 0 && split != 1 && split != 2 && split != 4 && split != 8) return SHARPY_EINVAL;
+  if (split != 0 && split != 1 && split != 2 && split != 4 && split != 8 && split != kSplitStaged)
+    return SHARPY_EINVAL;
   c->ll_split_forced = split;
   return SHARPY_OK;
 }

@@ -4,6 +4,7 @@
 // finishes with the lane-parallel epilogue. The instantiations of each
 // precision are compiled in their own unit (loglike_inst.cu).
 #pragma once
+#include "bulk.cuh"
 #include "context.cuh"
 #include "sweep.cuh"
 
@@ -108,6 +109,182 @@ loglike_kernel(DevModel m, DevEvent ev, int64_t n, const double* __restrict__ th
   }
 }
 
+// Staged variant for long segments on the mixed path (warps-per-vector
+// choice kSplitStaged): one vector per warp, kWarps vectors per CTA walking
+// the same bins in step. Each block of kStageBins bins of the tables comes
+// into shared memory by one bulk copy (two buffers, each completed on an
+// mbarrier) and is read there by all the CTA's vectors, instead of by each
+// vector from L2. The blocks are visited in the order of mixed_stream (stream
+// s: chunks s, s + kStreams, ...; the 8 blocks of a chunk in order), each
+// vector runs mixed_bin on the same bins in the same order and flushes at the
+// same chunk ends, and the streams are added in order in FP64: the moments
+// equal those of the other choices bit for bit.
+constexpr int kSplitStaged = 16;
+
+// The walk over the blocks for a CTA whose vectors' last active bin is kmax.
+struct StageWalk {
+  int kmax, st, c, b;
+  __device__ explicit StageWalk(int km) : kmax(km), st(0), c(0), b(0) {}
+  __device__ bool valid() const { return st < kStreams && c * kChunkBins + b * kStageBins <= kmax; }
+  __device__ int block() const { return c * (kChunkBins / kStageBins) + b; }
+  __device__ void next() {
+    if (++b < kChunkBins / kStageBins && c * kChunkBins + b * kStageBins <= kmax) return;
+    b = 0;
+    c += kStreams;
+    if (c * kChunkBins <= kmax) return;
+    c = ++st;
+  }
+};
+
+template <bool GRAD, int NDET>
+__global__ void __launch_bounds__(kWarps * 32, 2)
+loglike_staged_kernel(DevModel m, DevEvent ev, int64_t n, const double* __restrict__ theta, double* __restrict__ lnl,
+                      double* __restrict__ grad, int* status) {
+  constexpr int NACC = MomCount<NDET, GRAD>::value;
+  using FS = FlushShape<NACC>;
+  constexpr int NOUT = FS::KEEP;
+  constexpr int REC = stage_rec_bytes(NDET);
+  extern __shared__ __align__(128) unsigned char stage_buf[];  // two records
+  __shared__ __align__(8) uint64_t full[2];
+  __shared__ SweepCoef sc[kWarps];
+  __shared__ EpiCoef<float> ec[kWarps];
+  __shared__ float mom[kWarps][NDET * kNMom * 2];
+  __shared__ int kmax_s, abort_s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t base = (int64_t)blockIdx.x * kWarps;
+  const int D = m.n_dim;
+  if (warp == 0 && lane < kWarps) {
+    const int64_t p = base + lane;
+    if (p < n) {
+      double th[kMaxDim];
+      for (int i = 0; i < D; ++i) th[i] = theta[p * D + i];
+      prologue<float, GRAD, false>(m, ev, th, sc[lane], ec[lane]);
+    } else {
+      sc[lane].ok = 0;
+      sc[lane].kisco = -1;
+    }
+  }
+  for (int i = lane; i < NDET * kNMom * 2; i += 32) mom[warp][i] = 0.0f;
+  if (threadIdx.x == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    mbar_fence_init();
+    abort_s = 0;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    int km = (lane < kWarps && sc[lane].ok) ? sc[lane].kisco : -1;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) km = max(km, __shfl_xor_sync(0xffffffffu, km, o));
+    if (lane == 0) kmax_s = km;
+  }
+  __syncthreads();
+  const int kmax = kmax_s;
+  const bool live = sc[warp].ok != 0;
+  const int kend = live ? sc[warp].kisco : -1;
+  MixedCoef<NDET> P;
+  if (live) mixed_coef<NDET>(sc[warp], P);
+  // the first two blocks; then block i + 2 into the buffer that block i leaves
+  StageWalk issue(kmax);
+  int issued[2] = {0, 0};  // phases armed per buffer (thread 0)
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 2 && issue.valid(); ++q, issue.next()) {
+      mbar_arrive_expect_tx(&full[q], REC);
+      bulk_copy_g2s(stage_buf + q * REC, ev.stage + (size_t)issue.block() * REC, REC, &full[q]);
+      ++issued[q];
+    }
+  bool timed_out = false;
+  float acc[NACC], hi[NOUT], lo[NOUT];
+  double tot[NOUT];
+#pragma unroll
+  for (int t = 0; t < NOUT; ++t) tot[t] = 0.0;
+  int i = 0;  // blocks consumed
+  for (int st = 0; st < kStreams && st * kChunkBins <= kmax; ++st) {
+#pragma unroll
+    for (int t = 0; t < NOUT; ++t) hi[t] = lo[t] = 0.0f;
+    for (int c = st; c * kChunkBins <= kmax; c += kStreams) {
+      const bool mine = c * kChunkBins <= kend;  // a chunk of this vector's sweep
+#pragma unroll
+      for (int a = 0; a < NACC; ++a) acc[a] = 0.0f;
+      for (int b = 0; b < kChunkBins / kStageBins && c * kChunkBins + b * kStageBins <= kmax; ++b, ++i) {
+        const int buf = i & 1;
+        if (!timed_out && !mbar_wait(&full[buf], (uint32_t)(i >> 1) & 1u)) {
+          timed_out = true;
+          abort_s = 1;
+        }
+        const unsigned char* rec = stage_buf + buf * REC;
+        if (mine && !timed_out) {
+          for (int u = 0; u < kStageBins / 32; ++u) {
+            const int k0 = c * kChunkBins + b * kStageBins + u * 32;
+            if (k0 > kend) break;
+            const int k = k0 + lane;
+            if (k <= kend) mixed_bin<GRAD, NDET, false>(sc[warp], P, StagedBin{rec, u * 32 + lane}, acc);
+          }
+        }
+        __syncthreads();  // every warp is done with this buffer
+        if (threadIdx.x == 0 && issue.valid() && !abort_s) {
+          mbar_arrive_expect_tx(&full[buf], REC);
+          bulk_copy_g2s(stage_buf + buf * REC, ev.stage + (size_t)issue.block() * REC, REC, &full[buf]);
+          ++issued[buf];
+          issue.next();
+        }
+      }
+      if (mine) flush<NACC>(acc, hi, lo, lane);
+    }
+    if (st * kChunkBins <= kend)
+#pragma unroll
+      for (int t = 0; t < NOUT; ++t) tot[t] += (double)hi[t] + (double)lo[t];
+  }
+  if (timed_out) set_status(status, SHARPY_ETIMEOUT);
+  // after a timeout, wait (bounded) for the copies still in flight before the
+  // CTA's shared memory goes away
+  __syncthreads();
+  if (threadIdx.x == 0 && abort_s)
+    for (int q = 0; q < 2; ++q)
+      if (issued[q] > 0) mbar_wait(&full[q], (uint32_t)(issued[q] - 1) & 1u);
+  if (live && FS::owner(lane)) {
+#pragma unroll
+    for (int t = 0; t < NOUT; ++t) {
+      const int idx = FS::index(lane, t);
+      if (idx < NACC) mom[warp][acc_to_mom<NDET, GRAD>(idx)] = (float)tot[t];
+    }
+  }
+  __syncthreads();
+  if (warp == 0 && lane < kWarps) {
+    const int64_t q = base + lane;
+    if (q < n) {
+      double l = NAN, gph[SHARPY_NPHYS];
+      if (sc[lane].ok) epilogue<float, GRAD>(ev, sc[lane], ec[lane], mom[lane], &l, gph);
+      lnl[q] = l;
+      bool fin = isfinite(l);
+      if (GRAD) {
+        for (int d = 0; d < D; ++d) {
+          const double g = sc[lane].ok ? gph[m.phys[d]] : NAN;
+          grad[q * D + d] = g;
+          fin = fin && isfinite(g);
+        }
+      }
+      if (!fin) set_status(status, SHARPY_ENONFINITE);
+    }
+  }
+}
+
+template <bool GRAD, int NDET>
+inline cudaError_t launch_ll_staged(sharpy_ctx* c, int64_t n, const double* th, double* lnl, double* grad,
+                                    cudaStream_t s) {
+  constexpr int bytes = 2 * stage_rec_bytes(NDET);
+  const cudaError_t e =
+      cudaFuncSetAttribute(loglike_staged_kernel<GRAD, NDET>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  loglike_staged_kernel<GRAD, NDET><<<(unsigned)((n + kWarps - 1) / kWarps), kWarps * 32, bytes, s>>>(
+      c->model, c->ev, n, th, lnl, grad, c->d_status);
+  return cudaGetLastError();
+}
+
+// Defined in loglike_staged.cu (compiled as a unit of its own).
+cudaError_t launch_ll_staged_unit(sharpy_ctx* c, bool grad, int ndet, int64_t n, const double* th, double* lnl,
+                                  double* g, cudaStream_t s);
+
 template <int PREC, bool GRAD, int NDET, int SPLIT>
 inline void launch_ll_one(sharpy_ctx* c, int64_t n, const double* th, double* lnl, double* grad, cudaStream_t s) {
   constexpr int PPC = kWarps / SPLIT;
@@ -118,6 +295,12 @@ inline void launch_ll_one(sharpy_ctx* c, int64_t n, const double* th, double* ln
 template <int PREC, bool GRAD, int NDET>
 inline cudaError_t launch_ll_split(sharpy_ctx* c, int split, int64_t n, const double* th, double* lnl, double* grad,
                                    cudaStream_t s) {
+  if (split == kSplitStaged) {
+    if constexpr (PREC == SHARPY_MIXED) {
+      if (c->ev.stage) return launch_ll_staged_unit(c, GRAD, NDET, n, th, lnl, grad, s);
+    }
+    split = 8;  // no staged tables, or another precision: the 8-warp split
+  }
   switch (split) {
     case 2: launch_ll_one<PREC, GRAD, NDET, 2>(c, n, th, lnl, grad, s); break;
     case 4: launch_ll_one<PREC, GRAD, NDET, 4>(c, n, th, lnl, grad, s); break;

@@ -131,6 +131,168 @@ __device__ __forceinline__ float frac_turn(float x) {
 // bins (64 lane iterations: one FP32 block each) below k_ISCO, accumulated
 // into this lane's compensated outer sums hi, lo (kept lane-distributed as
 // the flush leaves them). Returns whether the stream had any bin.
+// Table values of one bin for the mixed sweep, from the SoA tables in global
+// memory (bin k).
+struct GlobalBin {
+  const DevEvent& ev;
+  int64_t K;
+  int k;
+  __device__ __forceinline__ float b32(int j) const { return __ldg(ev.b32 + (int64_t)j * K + k); }
+  __device__ __forceinline__ float b32lo(int j) const { return __ldg(ev.b32lo + (int64_t)j * K + k); }
+  __device__ __forceinline__ double b64(int j) const { return __ldg(ev.b64 + (int64_t)j * K + k); }
+  __device__ __forceinline__ float2 e32(int a) const { return __ldg(ev.e32 + (int64_t)a * K + k); }
+};
+
+// The same values from a staged record in shared memory (bin i of its block;
+// the mixed sweep's tables only: the split sweep also reads the large terms'
+// lo parts).
+struct StagedBin {
+  const unsigned char* rec;
+  int i;
+  __device__ __forceinline__ float b32(int j) const { return reinterpret_cast<const float*>(rec)[j * kStageBins + i]; }
+  __device__ __forceinline__ float b32lo(int j) const {
+    return reinterpret_cast<const float*>(rec + stage_off_lo())[stage_lo_row(j) * kStageBins + i];
+  }
+  __device__ __forceinline__ double b64(int j) const {
+    return reinterpret_cast<const double*>(rec + stage_off_b64())[stage_b64_row(j) * kStageBins + i];
+  }
+  __device__ __forceinline__ float2 e32(int a) const {
+    return reinterpret_cast<const float2*>(rec + stage_off_e32())[a * kStageBins + i];
+  }
+};
+
+// Per-particle constants of the mixed sweep, held in registers.
+template <int NDET>
+struct MixedCoef {
+  double al[kNPn];
+  double s0;
+  float ah[kNPn], alo[kNPn], th[NDET], tl[NDET];
+};
+
+template <int NDET>
+__device__ __forceinline__ void mixed_coef(const SweepCoef& sc, MixedCoef<NDET>& P) {
+#pragma unroll
+  for (int j = 0; j < kNPn; ++j) P.al[j] = sc.alpha[j];
+  P.s0 = sc.c0 + kTurnOffset;
+#pragma unroll
+  for (int j = 0; j < kNPn; ++j) {
+    P.ah[j] = sc.ahi[j];
+    P.alo[j] = sc.alo[j];
+  }
+#pragma unroll
+  for (int a = 0; a < NDET; ++a) {
+    P.th[a] = sc.thi[a];
+    P.tl[a] = sc.tlo[a];
+  }
+}
+
+// One bin of the mixed (or split) sweep: its phase, carrier and moment
+// updates, with the bin's table values from the loader ld (global memory or a
+// shared-memory stage: the same values, so the same sums).
+template <bool GRAD, int NDET, bool SPLIT, class L>
+__device__ __forceinline__ void mixed_bin(const SweepCoef& sc, const MixedCoef<NDET>& P, const L& ld, float* acc) {
+  const double (&al)[kNPn] = P.al;
+  const double s0 = P.s0;
+  const float (&ah)[kNPn] = P.ah;
+  const float (&alo)[kNPn] = P.alo;
+  const float (&th)[NDET] = P.th;
+  const float (&tl)[NDET] = P.tl;
+  float bf[kNBasis];
+  if (GRAD || SPLIT) {
+#pragma unroll
+    for (int j = 0; j < kNBasis; ++j) bf[j] = ld.b32(j);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) bf[small_pn(i)] = ld.b32(small_pn(i));
+    bf[8] = ld.b32(8);
+  }
+  const float fl = ld.b32lo(8);
+  // phase: FP64 accumulation on the turn offset, or split single precision
+  double S = s0;
+  int turn_s = 0;
+  float F = 0.0f, Sm = 0.0f;
+  if (!SPLIT) {
+    // the four terms that carry the large phase (Newtonian, 1PN, 1.5PN and
+    // the 2.5PN logarithm: up to ~2e3 turns on the long segment) accumulated
+    // in FP64 on the offset
+#pragma unroll
+    for (int i = 0; i < 4; ++i) S = fma(al[large_pn(i)], ld.b64(large_pn(i)), S);
+    turn_s = __double2loint(S);  // fractional turn of the large terms, 2^-32 units
+    // the four terms below ~8 turns (2PN, 3PN, its logarithm, 3.5PN) in FP32
+    // pairs: each product's integer turns removed exactly (FMA error term
+    // kept), the fractions summed pairwise in [-1/2, 1/2], then added to the
+    // FP64 part in 32-bit fixed point
+    float fr[4], er[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int j = small_pn(i);
+      const float bl = ld.b32lo(j);
+      const float p = __fmul_rn(ah[j], bf[j]);
+      fr[i] = frac_turn(p);
+      er[i] = fmaf(ah[j], bl, fmaf(alo[j], bf[j], fmaf(ah[j], bf[j], -p)));
+    }
+    const float f = frac_turn(__fadd_rn(frac_turn(__fadd_rn(fr[0], fr[1])), frac_turn(__fadd_rn(fr[2], fr[3]))));
+    const float q = frac_turn(__fadd_rn(f, __fadd_rn(__fadd_rn(er[0], er[1]), __fadd_rn(er[2], er[3]))));
+    turn_s += __float2int_rn(q * 4294967296.0f);  // wraps mod 1 turn
+  } else {
+    // sum_j alpha_j B_j mod 1: p = ahi*bhi is exact up to e (FMA), its integer
+    // part is removed exactly; the fractions are summed pairwise, reduced to
+    // [-1/2, 1/2] at every level (three levels instead of an eight-step
+    // chain), the error and cross terms likewise pairwise in Sm.
+    static_assert(kNPn == 8, "the pairwise tree below is written for eight basis terms");
+    float fr[kNPn], er[kNPn];
+#pragma unroll
+    for (int j = 0; j < kNPn; ++j) {
+      const float bl = ld.b32lo(j);
+      const float p = __fmul_rn(ah[j], bf[j]);
+      fr[j] = frac_turn(p);
+      er[j] = fmaf(ah[j], bl, fmaf(alo[j], bf[j], fmaf(ah[j], bf[j], -p)));
+    }
+    const float f01 = frac_turn(__fadd_rn(fr[0], fr[1])), f23 = frac_turn(__fadd_rn(fr[2], fr[3]));
+    const float f45 = frac_turn(__fadd_rn(fr[4], fr[5])), f67 = frac_turn(__fadd_rn(fr[6], fr[7]));
+    const float f03 = frac_turn(__fadd_rn(f01, f23)), f47 = frac_turn(__fadd_rn(f45, f67));
+    F = frac_turn(__fadd_rn(__fadd_rn(f03, f47), sc.c0f));
+    Sm = __fadd_rn(__fadd_rn(__fadd_rn(er[0], er[1]), __fadd_rn(er[2], er[3])),
+                   __fadd_rn(__fadd_rn(er[4], er[5]), __fadd_rn(er[6], er[7])));
+  }
+#pragma unroll
+  for (int a = 0; a < NDET; ++a) {
+    float ang;
+    if (!SPLIT) {
+      // f tau_a mod 1 from (thi + tlo)(fhi + flo): p = thi fhi is exact up
+      // to e (FMA), the other products are below 2^-20 turn
+      const float p = __fmul_rn(th[a], bf[8]);
+      const float e = fmaf(th[a], fl, fmaf(tl[a], bf[8], fmaf(th[a], bf[8], -p)));
+      const float q = frac_turn(__fadd_rn(frac_turn(p), e));  // [-1/2, 1/2] turn
+      const int turn = turn_s + __float2int_rn(q * 4294967296.0f);  // wraps mod 1 turn
+      ang = (float)turn * 1.46291807926715968e-9f;  // 2 pi / 2^32
+    } else {
+      const float p = __fmul_rn(th[a], bf[8]);
+      float Sa = Sm + fmaf(th[a], bf[8], -p);
+      Sa = fmaf(th[a], fl, fmaf(tl[a], bf[8], Sa));
+      const float Fa = frac_turn(__fadd_rn(F, frac_turn(p)));
+      ang = (Fa + Sa) * 6.28318530717958648f;
+    }
+    float sn, cs;
+    __sincosf(ang, &sn, &cs);
+    const float2 E = ld.e32(a);
+    const float zr = E.x * cs + E.y * sn;
+    const float zi = E.y * cs - E.x * sn;
+    if (GRAD) {
+#pragma unroll
+      for (int j = 0; j < kNBasis; ++j) {
+        acc[(a * kNMom + j) * 2] += zr * bf[j];
+        acc[(a * kNMom + j) * 2 + 1] += zi * bf[j];
+      }
+      acc[(a * kNMom + 9) * 2] += zr;
+      acc[(a * kNMom + 9) * 2 + 1] += zi;
+    } else {
+      acc[a * 2] += zr;
+      acc[a * 2 + 1] += zi;
+    }
+  }
+}
+
 template <bool GRAD, int NDET, bool SPLIT>
 __device__ bool mixed_stream(const DevEvent& ev, const SweepCoef& sc, int s, float* hi, float* lo) {
   constexpr int NACC = MomCount<NDET, GRAD>::value;
@@ -142,126 +304,18 @@ __device__ bool mixed_stream(const DevEvent& ev, const SweepCoef& sc, int s, flo
   for (int i = 0; i < NACC; ++i) acc[i] = 0.0f;
 #pragma unroll
   for (int i = 0; i < NOUT; ++i) hi[i] = lo[i] = 0.0f;
-  double al[kNPn];
-#pragma unroll
-  for (int j = 0; j < kNPn; ++j) al[j] = sc.alpha[j];
-  const double s0 = sc.c0 + kTurnOffset;
-  float ah[kNPn], alo[kNPn], th[NDET], tl[NDET];
-#pragma unroll
-  for (int j = 0; j < kNPn; ++j) {
-    ah[j] = sc.ahi[j];
-    alo[j] = sc.alo[j];
-  }
-#pragma unroll
-  for (int a = 0; a < NDET; ++a) {
-    th[a] = sc.thi[a];
-    tl[a] = sc.tlo[a];
-  }
+  MixedCoef<NDET> P;
+  mixed_coef<NDET>(sc, P);
   const int kend = sc.kisco;
   bool any = false;
   // Warp-uniform trip counts: lanes past k_ISCO idle but still join the flushes.
   for (int c = s; c * kChunkBins <= kend; c += kStreams) {
     any = true;
     for (int it = 0; it < kFlush; ++it) {
-    const int k0 = c * kChunkBins + it * 32;
-    if (k0 > kend) break;
-    const int k = k0 + lane;
-    if (k <= kend) {
-    float bf[kNBasis];
-    if (GRAD || SPLIT) {
-#pragma unroll
-      for (int j = 0; j < kNBasis; ++j) bf[j] = __ldg(ev.b32 + (int64_t)j * K + k);
-    } else {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) bf[small_pn(i)] = __ldg(ev.b32 + (int64_t)small_pn(i) * K + k);
-      bf[8] = __ldg(ev.b32 + (int64_t)8 * K + k);
-    }
-    const float fl = __ldg(ev.b32lo + (int64_t)8 * K + k);
-    // phase: FP64 accumulation on the turn offset, or split single precision
-    double S = s0;
-    int turn_s = 0;
-    float F = 0.0f, Sm = 0.0f;
-    if (!SPLIT) {
-      // the four terms that carry the large phase (Newtonian, 1PN, 1.5PN and
-      // the 2.5PN logarithm: up to ~2e3 turns on the long segment) accumulated
-      // in FP64 on the offset
-#pragma unroll
-      for (int i = 0; i < 4; ++i) S = fma(al[large_pn(i)], __ldg(ev.b64 + (int64_t)large_pn(i) * K + k), S);
-      turn_s = __double2loint(S);  // fractional turn of the large terms, 2^-32 units
-      // the four terms below ~8 turns (2PN, 3PN, its logarithm, 3.5PN) in FP32
-      // pairs: each product's integer turns removed exactly (FMA error term
-      // kept), the fractions summed pairwise in [-1/2, 1/2], then added to the
-      // FP64 part in 32-bit fixed point
-      float fr[4], er[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int j = small_pn(i);
-        const float bl = __ldg(ev.b32lo + (int64_t)j * K + k);
-        const float p = __fmul_rn(ah[j], bf[j]);
-        fr[i] = frac_turn(p);
-        er[i] = fmaf(ah[j], bl, fmaf(alo[j], bf[j], fmaf(ah[j], bf[j], -p)));
-      }
-      const float f = frac_turn(__fadd_rn(frac_turn(__fadd_rn(fr[0], fr[1])), frac_turn(__fadd_rn(fr[2], fr[3]))));
-      const float q = frac_turn(__fadd_rn(f, __fadd_rn(__fadd_rn(er[0], er[1]), __fadd_rn(er[2], er[3]))));
-      turn_s += __float2int_rn(q * 4294967296.0f);  // wraps mod 1 turn
-    } else {
-      // sum_j alpha_j B_j mod 1: p = ahi*bhi is exact up to e (FMA), its integer
-      // part is removed exactly; the fractions are summed pairwise, reduced to
-      // [-1/2, 1/2] at every level (three levels instead of an eight-step
-      // chain), the error and cross terms likewise pairwise in Sm.
-      static_assert(kNPn == 8, "the pairwise tree below is written for eight basis terms");
-      float fr[kNPn], er[kNPn];
-#pragma unroll
-      for (int j = 0; j < kNPn; ++j) {
-        const float bl = __ldg(ev.b32lo + (int64_t)j * K + k);
-        const float p = __fmul_rn(ah[j], bf[j]);
-        fr[j] = frac_turn(p);
-        er[j] = fmaf(ah[j], bl, fmaf(alo[j], bf[j], fmaf(ah[j], bf[j], -p)));
-      }
-      const float f01 = frac_turn(__fadd_rn(fr[0], fr[1])), f23 = frac_turn(__fadd_rn(fr[2], fr[3]));
-      const float f45 = frac_turn(__fadd_rn(fr[4], fr[5])), f67 = frac_turn(__fadd_rn(fr[6], fr[7]));
-      const float f03 = frac_turn(__fadd_rn(f01, f23)), f47 = frac_turn(__fadd_rn(f45, f67));
-      F = frac_turn(__fadd_rn(__fadd_rn(f03, f47), sc.c0f));
-      Sm = __fadd_rn(__fadd_rn(__fadd_rn(er[0], er[1]), __fadd_rn(er[2], er[3])),
-                     __fadd_rn(__fadd_rn(er[4], er[5]), __fadd_rn(er[6], er[7])));
-    }
-#pragma unroll
-    for (int a = 0; a < NDET; ++a) {
-      float ang;
-      if (!SPLIT) {
-        // f tau_a mod 1 from (thi + tlo)(fhi + flo): p = thi fhi is exact up
-        // to e (FMA), the other products are below 2^-20 turn
-        const float p = __fmul_rn(th[a], bf[8]);
-        const float e = fmaf(th[a], fl, fmaf(tl[a], bf[8], fmaf(th[a], bf[8], -p)));
-        const float q = frac_turn(__fadd_rn(frac_turn(p), e));  // [-1/2, 1/2] turn
-        const int turn = turn_s + __float2int_rn(q * 4294967296.0f);  // wraps mod 1 turn
-        ang = (float)turn * 1.46291807926715968e-9f;  // 2 pi / 2^32
-      } else {
-        const float p = __fmul_rn(th[a], bf[8]);
-        float Sa = Sm + fmaf(th[a], bf[8], -p);
-        Sa = fmaf(th[a], fl, fmaf(tl[a], bf[8], Sa));
-        const float Fa = frac_turn(__fadd_rn(F, frac_turn(p)));
-        ang = (Fa + Sa) * 6.28318530717958648f;
-      }
-      float sn, cs;
-      __sincosf(ang, &sn, &cs);
-      const float2 E = __ldg(ev.e32 + (int64_t)a * K + k);
-      const float zr = E.x * cs + E.y * sn;
-      const float zi = E.y * cs - E.x * sn;
-      if (GRAD) {
-#pragma unroll
-        for (int j = 0; j < kNBasis; ++j) {
-          acc[(a * kNMom + j) * 2] += zr * bf[j];
-          acc[(a * kNMom + j) * 2 + 1] += zi * bf[j];
-        }
-        acc[(a * kNMom + 9) * 2] += zr;
-        acc[(a * kNMom + 9) * 2 + 1] += zi;
-      } else {
-        acc[a * 2] += zr;
-        acc[a * 2 + 1] += zi;
-      }
-    }
-    }
+      const int k0 = c * kChunkBins + it * 32;
+      if (k0 > kend) break;
+      const int k = k0 + lane;
+      if (k <= kend) mixed_bin<GRAD, NDET, SPLIT>(sc, P, GlobalBin{ev, K, k}, acc);
     }
     flush<NACC>(acc, hi, lo, lane);
   }

@@ -19,7 +19,8 @@ namespace sharpy {
 
 constexpr int kSlotChoices[] = {8, 16, 32};
 constexpr int kNumSlotChoices = 3;
-// Warps that share one particle's sweep in the standalone likelihood kernel.
+// Warps that share one particle's sweep in the standalone likelihood kernel
+// (plus the staged kernel, choice 16, on long segments of the mixed path).
 constexpr int kSplitChoices[] = {1, 2, 4, 8};
 constexpr int kNumSplitChoices = 4;
 

@@ -235,17 +235,19 @@ def test_autograd_backward_is_the_adjoint():
 def test_loglike_split_factor_invariant(wname):
     """The likelihood kernel cuts a vector's bins into chunks of 2048 dealt to 8 streams merged in a fixed
     order, so the number of warps sharing a vector (1, 2, 4, 8: the tuner's choice) does not change ln L or
-    the gradient, bit for bit, on every path; on the 259585-bin segment the streams' merge stays within the
+    the gradient, bit for bit, on every path; nor does choice 16, the staged kernel (one vector per warp, the
+    tables of each 256-bin block brought into shared memory by one bulk copy), which the 259585-bin segment's
+    mixed path has and the others replace by 8. On that segment the streams' merge stays within the
     long-signal tolerance of the oracle. The tuner's pick is one of the candidates."""
     G.require_gpu()
     w = getattr(inputs, wname)()
     ev, ctx, th_inj, _ = G.event_pair(w)
-    n = 40
-    th = np.vstack([inputs.prior_draws(w, n // 2, 6), inputs.ball(w, th_inj, n // 2, 7)])
+    n = 37  # a ragged last CTA (the staged kernel holds 8 vectors a CTA)
+    th = np.vstack([inputs.prior_draws(w, 19, 6), inputs.ball(w, th_inj, n - 19, 7)])
     t = G.to_dev(th)
     for prec in ("fp64", "mixed", "split"):
         ref = None
-        for split in (1, 2, 4, 8):
+        for split in (1, 2, 4, 8, 16):
             ctx.set_loglike_split(split)
             l, g = ctx.loglike_grad(t, prec)
             if ref is None:
@@ -257,5 +259,5 @@ def test_loglike_split_factor_invariant(wname):
             assert np.max(np.abs(ref[0].cpu().numpy()[:4] - lref)) <= 1e-2
     ctx.set_loglike_split(0)
     ctx.loglike_grad(t, "mixed")
-    assert ctx.loglike_split(n, "mixed") in (1, 2, 4, 8)
+    assert ctx.loglike_split(n, "mixed") in ((1, 2, 4, 8, 16) if wname == "bns" else (1, 2, 4, 8))
     assert ctx.status() == 0
