@@ -452,6 +452,8 @@ def main_loglike_launch(args):
     ctx, th_inj, _ = api.make_event(w, seed=0)
     n = args.particles or w.n_particles
     th = torch.tensor(inputs.ball(w, th_inj, n, 2, rel=1e-3), dtype=torch.float64, device="cuda")
+    if args.split:
+        ctx.set_loglike_split(args.split)  # no tuning launches: the first call is one launch
     ctx.loglike_grad(th, args.precision)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -461,6 +463,7 @@ def main_loglike_launch(args):
     torch.cuda.synchronize()
     act = float(_active_bins(w, th.cpu().numpy()).sum())
     print(json.dumps({"mode": "loglike_launch", "workload": w.name, "precision": args.precision, "particles": n,
+                      "split": ctx.loglike_split(n, args.precision) if not args.split else args.split,
                       "ms": e0.elapsed_time(e1), "active_bin_det": act, "status": ctx.status()}))
     return 0
 
@@ -566,6 +569,8 @@ def main():
     ap.add_argument("--workload", default="bbh11", choices=["tiny", "bbh11", "bbh11_long", "bns", "batch64"])
     ap.add_argument("--mode", default="smc", choices=["smc", "loglike", "nuts_launch", "loglike_launch"])
     ap.add_argument("--particles", type=int, default=0, help="loglike_launch: vectors per call (0: the workload's)")
+    ap.add_argument("--split", type=int, default=0, choices=[0, 1, 2, 4, 8, 16],
+                    help="loglike_launch: warps per vector, 16 = the staged kernel (0: tuned)")
     ap.add_argument("--ensemble", default=None, choices=["first", "late"], help="nuts_launch: one ensemble only")
     ap.add_argument("--slots", type=int, default=0, choices=[0, 8, 16, 32],
                     help="batch64: NUTS particles per CTA (0: autotuned)")
