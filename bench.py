@@ -63,25 +63,29 @@ WORK = {p: work(p) for p in ("mixed", "split", "fp64")}
 # were taken on (reported while the sources' hash matches, else the estimates
 # above and traffic null). From one ncu launch each (`--mode nuts_launch
 # --ensemble late` for the NUTS kernel on the 11-D workload, `--mode
-# loglike_launch --workload bns --particles 1024` for the likelihood kernel):
+# loglike_launch` with the tuned `--split` for the likelihood kernels):
 # FP64 FLOP = 2 DFMA + DADD + DMUL and FP32 FLOP = 2 FFMA + FADD + FMUL thread
 # instructions (smsp__sass_thread_inst_executed_op_*_pred_on.sum) per active
 # (bin, detector), and DRAM bytes read + written per launch.
-COUNTED_SOURCES = ["nuts_kernel.cuh", "sweep.cuh", "physics.cuh", "common.cuh", "dfloat.cuh", "loglike_kernel.cuh"]
-COUNTED = {"sources_sha256_16": "4fc80ab8d879d02e",
+COUNTED_SOURCES = ["nuts_kernel.cuh", "sweep.cuh", "physics.cuh", "common.cuh", "dfloat.cuh", "loglike_kernel.cuh",
+                   "bulk.cuh"]
+COUNTED = {"sources_sha256_16": "7fe00f912feba62e",
            "nuts": {"mixed": {"fp64": 2.9620, "fp32": 107.01},
                     "split": {"fp64": 0.2756, "fp32": 126.67},
                     "fp64": {"fp64": 110.50, "fp32": 0.0152}},
-           # the likelihood kernel: one call on 1024 vectors near the injection of
-           # the 259585-bin segment (the tuned 8 / 4 warps per vector)
-           "loglike": {"mixed": {"fp64": 2.6689, "fp32": 81.405},
-                       "fp64": {"fp64": 90.365, "fp32": 0.0}},
-           "traffic": {"mixed": 3839232, "split": 3805440, "fp64": 4508160},
+           # the likelihood kernels, one call each with the tuner's choice for
+           # that shape: 2048 vectors of the 11-D workload (1 warp per vector),
+           # 8192 vectors of the 259585-bin segment (mixed: the staged kernel;
+           # FP64: 4 warps per vector)
+           "loglike": {"bbh11": {"mixed": {"fp64": 2.8057, "fp32": 88.321}},
+                       "bns": {"mixed": {"fp64": 2.6686, "fp32": 81.405},
+                               "fp64": {"fp64": 90.365, "fp32": 0.0}}},
+           "traffic": {"mixed": 3951104, "split": 4042240, "fp64": 4601600},
            # the same captures: FP64 pipe busy, warps active and issue active
            # (sm__inst_executed_pipe_fp64, sm__warps_active,
            # smsp__issue_active; % of peak sustained active)
-           "util": {"mixed": {"fp64_pipe": 34.3, "warps_active": 10.7, "issue_active": 36.8},
-                    "split": {"fp64_pipe": 16.8, "warps_active": 10.7, "issue_active": 40.5},
+           "util": {"mixed": {"fp64_pipe": 34.4, "warps_active": 10.7, "issue_active": 37.0},
+                    "split": {"fp64_pipe": 16.6, "warps_active": 10.7, "issue_active": 40.2},
                     "fp64": {"fp64_pipe": 86.0, "warps_active": 11.0, "issue_active": 8.0}}}
 
 
@@ -94,10 +98,11 @@ def _sources_hash():
     return h.hexdigest()[:16]
 
 
-def counted(kernel, precision):
-    """(fp64 FLOP, fp32 FLOP, source) per active (bin, detector) of `kernel` ('nuts' or 'loglike')."""
-    if COUNTED["sources_sha256_16"] == _sources_hash() and precision in COUNTED[kernel]:
-        c = COUNTED[kernel][precision]
+def counted(kernel, precision, workload="bbh11"):
+    """(fp64 FLOP, fp32 FLOP, source) per active (bin, detector) of `kernel` ('nuts', or 'loglike' on `workload`)."""
+    table = COUNTED[kernel] if kernel == "nuts" else COUNTED[kernel].get(workload, {})
+    if COUNTED["sources_sha256_16"] == _sources_hash() and precision in table:
+        c = table[precision]
         return c["fp64"], c["fp32"], "ncu instruction counts of this kernel's sources"
     wk = WORK[precision]
     f64 = wk["flop"] if wk["pipe"] == "fp64" else 0.0
@@ -299,7 +304,7 @@ def main_loglike(args):
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
-            f64c, f32c, fsrc = counted("loglike", prec)
+            f64c, f32c, fsrc = counted("loglike", prec, w.name)
             pipe, flop, peak = binding_pipe(f64c, f32c, peaks[1], peaks[0])
             tfl = n * act * flop / (ms * 1e-3) / 1e12
             row[prec] = {"evals_per_s": n / (ms * 1e-3), "ms_per_call": ms, "pipe": pipe,
