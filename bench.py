@@ -67,9 +67,11 @@ WORK = {p: work(p) for p in ("mixed", "split", "fp64")}
 # FP64 FLOP = 2 DFMA + DADD + DMUL and FP32 FLOP = 2 FFMA + FADD + FMUL thread
 # instructions (smsp__sass_thread_inst_executed_op_*_pred_on.sum) per active
 # (bin, detector), and DRAM bytes read + written per launch.
-COUNTED_SOURCES = ["nuts_kernel.cuh", "sweep.cuh", "physics.cuh", "common.cuh", "dfloat.cuh", "loglike_kernel.cuh",
-                   "bulk.cuh"]
-COUNTED = {"sources_sha256_16": "7fe00f912feba62e",
+# Each kernel's counts are keyed to the device-code files its instructions
+# come from (context.cuh, the host-side context, is not among them).
+COUNTED_SOURCES = {"nuts": ["nuts_kernel.cuh", "sweep.cuh", "physics.cuh", "common.cuh", "dfloat.cuh"],
+                   "loglike": ["loglike_kernel.cuh", "bulk.cuh", "sweep.cuh", "physics.cuh", "common.cuh", "dfloat.cuh"]}
+COUNTED = {"sources_sha256_16": {"nuts": "7d19c13975e59d1e", "loglike": "35e895237a35d5c7"},
            "nuts": {"mixed": {"fp64": 2.9620, "fp32": 107.01},
                     "split": {"fp64": 0.2756, "fp32": 126.67},
                     "fp64": {"fp64": 110.50, "fp32": 0.0152}},
@@ -89,10 +91,10 @@ COUNTED = {"sources_sha256_16": "7fe00f912feba62e",
                     "fp64": {"fp64_pipe": 86.0, "warps_active": 11.0, "issue_active": 8.0}}}
 
 
-def _sources_hash():
+def _sources_hash(kernel="nuts"):
     import hashlib
     h = hashlib.sha256()
-    for f in COUNTED_SOURCES:
+    for f in COUNTED_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_2601_02336_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -101,23 +103,24 @@ def _sources_hash():
 def counted(kernel, precision, workload="bbh11"):
     """(fp64 FLOP, fp32 FLOP, source) per active (bin, detector) of `kernel` ('nuts', or 'loglike' on `workload`)."""
     table = COUNTED[kernel] if kernel == "nuts" else COUNTED[kernel].get(workload, {})
-    if COUNTED["sources_sha256_16"] == _sources_hash() and precision in table:
+    same = COUNTED["sources_sha256_16"][kernel] == _sources_hash(kernel)
+    if same and precision in table:
         c = table[precision]
         return c["fp64"], c["fp32"], "ncu instruction counts of this kernel's sources"
     wk = WORK[precision]
     f64 = wk["flop"] if wk["pipe"] == "fp64" else 0.0
-    why = "sources changed since the counts" if COUNTED["sources_sha256_16"] != _sources_hash() else "no counts recorded"
+    why = "no counts recorded" if same else "sources changed since the counts"
     return f64, wk["fp32_flop"] if wk["pipe"] == "fp64" else wk["flop"], f"hand estimate ({why})"
 
 
 def _traffic(precision):
-    if COUNTED["sources_sha256_16"] != _sources_hash():
+    if COUNTED["sources_sha256_16"]["nuts"] != _sources_hash("nuts"):
         return None
     return COUNTED["traffic"].get(precision)
 
 
 def _util(precision):
-    if COUNTED["sources_sha256_16"] != _sources_hash():
+    if COUNTED["sources_sha256_16"]["nuts"] != _sources_hash("nuts"):
         return None
     return COUNTED["util"].get(precision)
 

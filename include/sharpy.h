@@ -195,6 +195,14 @@ int sharpy_loglike_split(sharpy_ctx* ctx, int64_t n, int precision, int with_gra
    sharpy_loglike_grad call of the context instead of the tuned choice; 0
    returns to tuning. SHARPY_EINVAL for other values. */
 int sharpy_set_loglike_split(sharpy_ctx* ctx, int split);
+/* Failure-detection tests of the staged kernel (choice 16): its bulk copy of
+   table block `skip_block` is left out (-1: none), so the mbarrier waits for
+   that block run out, and each wait polls at most `wait_polls` times (0: the
+   default bound). A wait that runs out records SHARPY_ETIMEOUT in the status
+   word; the kernel issues no further copies, waits (bounded) for the copies in
+   flight and returns, and the context stays usable. SHARPY_EINVAL for
+   skip_block < -1 or wait_polls < 0. */
+int sharpy_set_stage_test_hooks(sharpy_ctx* ctx, int skip_block, int wait_polls);
 
 /* Detector-frame strain h_a(f_k) [N][n_det][n_bins][2] (device) of N
    parameter vectors (used to build injections). FP64. TaylorF2 only. */

@@ -132,6 +132,12 @@ class Context:
         it does not apply), in later likelihood calls (0: tune)."""
         check(lib().sharpy_set_loglike_split(self._h, int(split)), "sharpy_set_loglike_split")
 
+    def set_stage_test_hooks(self, skip_block=-1, wait_polls=0):
+        """Failure-detection tests of the staged likelihood kernel: leave out the bulk copy of table block
+        `skip_block` (-1: none) and poll each mbarrier wait at most `wait_polls` times (0: the default)."""
+        check(lib().sharpy_set_stage_test_hooks(self._h, int(skip_block), int(wait_polls)),
+              "sharpy_set_stage_test_hooks")
+
     def waveform(self, theta):
         theta = _dev(theta, "theta")
         h = torch.empty((theta.shape[0], self.n_det, self.n_bins, 2), dtype=torch.float64,

@@ -42,10 +42,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 
-// Bounded wait: false if the phase did not complete within the bound (the
-// caller reports SHARPY_ETIMEOUT instead of spinning for ever).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (int t = 0; t < (1 << 20); ++t)
+// Bounded wait of at most `polls` try-waits (each may suspend for a short,
+// hardware-defined time): false if the phase did not complete within the
+// bound (the caller reports SHARPY_ETIMEOUT instead of spinning for ever).
+constexpr int kMbarWaitPolls = 1 << 20;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int polls = kMbarWaitPolls) {
+  for (int t = 0; t < polls; ++t)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }

@@ -52,8 +52,12 @@ struct sharpy_ctx {
   double* d_p2 = nullptr;       // [n_det][kNBasis (kNBasis + 1) / 2][K] prefix sums of w f^-7/3 B_m B_n
   // NUTS slot count picked by the autotuner, per precision and metric kind
   // (shared / per-particle), for tuned_n[p][l] particles (0: not tuned)
-  int64_t nuts_tick_limit = 0;
-  int64_t first_id = 0;         // ensemble index of row 0 of the particle arrays (sharpy_set_shard)  // > 0: lowered NUTS tick bound (sharpy_set_nuts_tick_limit)
+  int64_t nuts_tick_limit = 0;  // > 0: lowered NUTS tick bound (sharpy_set_nuts_tick_limit)
+  int64_t first_id = 0;         // ensemble index of row 0 of the particle arrays (sharpy_set_shard)
+  // staged likelihood kernel, failure-detection tests (sharpy_set_stage_test_hooks): the block whose bulk copy
+  // is left out (-1: none) and the mbarrier wait bound in polls (0: the default)
+  int stage_skip_block = -1;
+  int stage_wait_polls = 0;
   int tuned_slots[3][2] = {};
   // likelihood kernel: warps per particle picked per call shape (loglike.cu)
   std::vector<LoglikeTuned> ll_tuned;

@@ -162,6 +162,15 @@ int sharpy_set_loglike_split(sharpy_ctx* c, int split) {
   return SHARPY_OK;
 }
 
+int sharpy_set_stage_test_hooks(sharpy_ctx* c, int skip_block, int wait_polls) {
+  int rc = check_ctx(c, false);
+  if (rc) return rc;
+  if (skip_block < -1 || wait_polls < 0) return SHARPY_EINVAL;
+  c->stage_skip_block = skip_block;
+  c->stage_wait_polls = wait_polls;
+  return SHARPY_OK;
+}
+
 int sharpy_loglike_split(sharpy_ctx* c, int64_t n, int precision, int with_grad) {
   int rc = check_ctx(c, true);
   if (rc) return rc;

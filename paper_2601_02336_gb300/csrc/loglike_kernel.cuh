@@ -139,7 +139,7 @@ struct StageWalk {
 template <bool GRAD, int NDET>
 __global__ void __launch_bounds__(kWarps * 32, 2)
 loglike_staged_kernel(DevModel m, DevEvent ev, int64_t n, const double* __restrict__ theta, double* __restrict__ lnl,
-                      double* __restrict__ grad, int* status) {
+                      double* __restrict__ grad, int* status, int skip_block, int wait_polls) {
   constexpr int NACC = MomCount<NDET, GRAD>::value;
   using FS = FlushShape<NACC>;
   constexpr int NOUT = FS::KEEP;
@@ -187,8 +187,11 @@ loglike_staged_kernel(DevModel m, DevEvent ev, int64_t n, const double* __restri
   // the first two blocks; then block i + 2 into the buffer that block i leaves
   StageWalk issue(kmax);
   int issued[2] = {0, 0};  // phases armed per buffer (thread 0)
+  // skip_block (failure-detection tests only): that block's copy is left out,
+  // so the waits for it run out
   if (threadIdx.x == 0)
     for (int q = 0; q < 2 && issue.valid(); ++q, issue.next()) {
+      if (issue.block() == skip_block) continue;
       mbar_arrive_expect_tx(&full[q], REC);
       bulk_copy_g2s(stage_buf + q * REC, ev.stage + (size_t)issue.block() * REC, REC, &full[q]);
       ++issued[q];
@@ -208,7 +211,7 @@ loglike_staged_kernel(DevModel m, DevEvent ev, int64_t n, const double* __restri
       for (int a = 0; a < NACC; ++a) acc[a] = 0.0f;
       for (int b = 0; b < kChunkBins / kStageBins && c * kChunkBins + b * kStageBins <= kmax; ++b, ++i) {
         const int buf = i & 1;
-        if (!timed_out && !mbar_wait(&full[buf], (uint32_t)(i >> 1) & 1u)) {
+        if (!timed_out && !mbar_wait(&full[buf], (uint32_t)(i >> 1) & 1u, wait_polls)) {
           timed_out = true;
           abort_s = 1;
         }
@@ -223,9 +226,11 @@ loglike_staged_kernel(DevModel m, DevEvent ev, int64_t n, const double* __restri
         }
         __syncthreads();  // every warp is done with this buffer
         if (threadIdx.x == 0 && issue.valid() && !abort_s) {
-          mbar_arrive_expect_tx(&full[buf], REC);
-          bulk_copy_g2s(stage_buf + buf * REC, ev.stage + (size_t)issue.block() * REC, REC, &full[buf]);
-          ++issued[buf];
+          if (issue.block() != skip_block) {
+            mbar_arrive_expect_tx(&full[buf], REC);
+            bulk_copy_g2s(stage_buf + buf * REC, ev.stage + (size_t)issue.block() * REC, REC, &full[buf]);
+            ++issued[buf];
+          }
           issue.next();
         }
       }
@@ -236,12 +241,13 @@ loglike_staged_kernel(DevModel m, DevEvent ev, int64_t n, const double* __restri
       for (int t = 0; t < NOUT; ++t) tot[t] += (double)hi[t] + (double)lo[t];
   }
   if (timed_out) set_status(status, SHARPY_ETIMEOUT);
-  // after a timeout, wait (bounded) for the copies still in flight before the
-  // CTA's shared memory goes away
+  // after a timeout, wait (bounded, with the full bound whatever wait_polls
+  // says) for the copies still in flight before the CTA's shared memory goes
+  // away: they were all issued, in bounds, so they land
   __syncthreads();
   if (threadIdx.x == 0 && abort_s)
     for (int q = 0; q < 2; ++q)
-      if (issued[q] > 0) mbar_wait(&full[q], (uint32_t)(issued[q] - 1) & 1u);
+      if (issued[q] > 0) mbar_wait(&full[q], (uint32_t)(issued[q] - 1) & 1u, kMbarWaitPolls);
   if (live && FS::owner(lane)) {
 #pragma unroll
     for (int t = 0; t < NOUT; ++t) {
@@ -277,7 +283,8 @@ inline cudaError_t launch_ll_staged(sharpy_ctx* c, int64_t n, const double* th, 
       cudaFuncSetAttribute(loglike_staged_kernel<GRAD, NDET>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
   loglike_staged_kernel<GRAD, NDET><<<(unsigned)((n + kWarps - 1) / kWarps), kWarps * 32, bytes, s>>>(
-      c->model, c->ev, n, th, lnl, grad, c->d_status);
+      c->model, c->ev, n, th, lnl, grad, c->d_status, c->stage_skip_block,
+      c->stage_wait_polls > 0 ? c->stage_wait_polls : kMbarWaitPolls);
   return cudaGetLastError();
 }
 

@@ -14,6 +14,7 @@ import torch
 
 import oracle
 from paper_2601_02336_gb300 import api, inputs
+from paper_2601_02336_gb300 import _lib
 from paper_2601_02336_gb300._lib import SharpyError
 from tests import gpu_helpers as G
 from tests import helpers
@@ -261,3 +262,28 @@ def test_loglike_split_factor_invariant(wname):
     ctx.loglike_grad(t, "mixed")
     assert ctx.loglike_split(n, "mixed") in ((1, 2, 4, 8, 16) if wname == "bns" else (1, 2, 4, 8))
     assert ctx.status() == 0
+
+
+def test_staged_kernel_wait_timeout_reports_status():
+    """Failure detection without a fault in the staged kernel (choice 16). The test hook leaves out the bulk copy of
+    one table block, so the mbarrier waits for it run out after a short poll bound. The call returns; the status word
+    reads SHARPY_ETIMEOUT, and the kernel issued no further copies and drained the ones in flight. The same context then
+    runs clean: status 0 and ln L and gradient equal, bit for bit, to the 1-warp split kernel's."""
+    G.require_gpu()
+    w = inputs.bns()
+    ctx, th_inj, _ = api.make_event(w, seed=0)
+    t = G.to_dev(inputs.ball(w, th_inj, 20, 5, rel=1e-3))
+    ctx.set_loglike_split(1)
+    ref_l, ref_g = ctx.loglike_grad(t, "mixed")
+    assert ctx.status() == 0
+    ctx.set_loglike_split(16)
+    ctx.set_stage_test_hooks(skip_block=3, wait_polls=64)
+    ctx.loglike_grad(t, "mixed")
+    torch.cuda.synchronize()
+    assert ctx.status() == _lib.ETIMEOUT
+    ctx.clear_status()
+    ctx.set_stage_test_hooks(-1, 0)
+    l, g = ctx.loglike_grad(t, "mixed")
+    assert ctx.status() == 0
+    assert torch.equal(l, ref_l) and torch.equal(g, ref_g)
+    ctx.set_loglike_split(0)
