@@ -27,9 +27,11 @@
  * library's moment-based adjoint.
  *
  * Parity pins live in tests/ (closed forms, finite differences, analytic
- * evidences, brute force). Functions without a pin: the physical value of
- * the self-spin coefficient in sigma ("parity unpinned": only the formula
- * as written is checked).
+ * evidences, brute force; the PN phase coefficients, sigma included, through
+ * the chirp time against the published TaylorT2 series and an energy-balance
+ * derivation). Parity unpinned: the constant phase terms (the "1" of
+ * 1 + 3 ln(v / v_lso) and v_lso itself), which shift Psi by a constant that
+ * phi_c absorbs; only the formula as written is checked.
  */
 #ifndef SHARPY_ORACLE_H
 #define SHARPY_ORACLE_H
