@@ -71,7 +71,7 @@ WORK = {p: work(p) for p in ("mixed", "split", "fp64")}
 # come from (context.cuh, the host-side context, is not among them).
 COUNTED_SOURCES = {"nuts": ["nuts_kernel.cuh", "sweep.cuh", "physics.cuh", "common.cuh", "dfloat.cuh"],
                    "loglike": ["loglike_kernel.cuh", "bulk.cuh", "sweep.cuh", "physics.cuh", "common.cuh", "dfloat.cuh"]}
-COUNTED = {"sources_sha256_16": {"nuts": "7d19c13975e59d1e", "loglike": "35e895237a35d5c7"},
+COUNTED = {"sources_sha256_16": {"nuts": "4c9bc0a722a82040", "loglike": "35e895237a35d5c7"},
            "nuts": {"mixed": {"fp64": 2.9620, "fp32": 107.01},
                     "split": {"fp64": 0.2756, "fp32": 126.67},
                     "fp64": {"fp64": 110.50, "fp32": 0.0152}},
@@ -82,7 +82,7 @@ COUNTED = {"sources_sha256_16": {"nuts": "7d19c13975e59d1e", "loglike": "35e8952
            "loglike": {"bbh11": {"mixed": {"fp64": 2.8057, "fp32": 88.321}},
                        "bns": {"mixed": {"fp64": 2.6686, "fp32": 81.405},
                                "fp64": {"fp64": 90.365, "fp32": 0.0}}},
-           "traffic": {"mixed": 3951104, "split": 4042240, "fp64": 4601600},
+           "traffic": {"mixed": 3830016, "split": 3913984, "fp64": 4599040},
            # the same captures: FP64 pipe busy, warps active and issue active
            # (sm__inst_executed_pipe_fp64, sm__warps_active,
            # smsp__issue_active; % of peak sustained active)
@@ -416,6 +416,8 @@ def main_nuts_launch(args):
     sets = {"first": (inputs.prior_draws(w, w.n_particles, 1), 1e-4),
             "late": (inputs.ball(w, th_inj, w.n_particles, 2, rel=1e-3), 1.0)}
     names = [args.ensemble] if args.ensemble else list(sets)
+    if args.slots:
+        ctx.set_nuts_slots(args.slots)
     stream = torch.cuda.current_stream()
     out = {"mode": "nuts_launch", "workload": _describe(w), "precision": args.precision, "ensembles": {}}
     for name in names:
@@ -580,8 +582,8 @@ def main():
     ap.add_argument("--split", type=int, default=0, choices=[0, 1, 2, 4, 8, 16],
                     help="loglike_launch: warps per vector, 16 = the staged kernel (0: tuned)")
     ap.add_argument("--ensemble", default=None, choices=["first", "late"], help="nuts_launch: one ensemble only")
-    ap.add_argument("--slots", type=int, default=0, choices=[0, 8, 16, 32],
-                    help="batch64: NUTS particles per CTA (0: autotuned)")
+    ap.add_argument("--slots", type=int, default=0, choices=[0, 4, 8, 16, 32],
+                    help="batch64 and nuts_launch: NUTS particles per CTA (0: autotuned / default)")
     ap.add_argument("--metric", type=int, default=None, choices=[0, 1, 2],
                     help="NUTS metric (default: the workload's): 0 identity, 1 covariance, 2 per-particle local")
     args = ap.parse_args()

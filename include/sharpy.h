@@ -245,6 +245,13 @@ int sharpy_nuts_mutate_cov_step(sharpy_ctx* ctx, int64_t n, double beta, double*
    for max_ticks < 0. */
 int sharpy_set_nuts_tick_limit(sharpy_ctx* ctx, int64_t max_ticks);
 
+/* NUTS particle slots per CTA (4, 8, 16 or 32) for the context's later
+   single-event launches (sharpy_nuts_mutate*, sharpy_smc_run, which then
+   skips its slot tuning) instead of the tuned or default choice; 0 returns to
+   those. A NUTS result does not depend on the slot count. SHARPY_EINVAL for
+   other values. */
+int sharpy_set_nuts_slots(sharpy_ctx* ctx, int slots);
+
 /* Particle sharding of one event over several GPUs (one context per GPU,
    Sec. 7 names splitting the particles across devices as the way to scale
    out): the particle arrays given to this context's later prior draws and
@@ -370,13 +377,13 @@ int sharpy_batch_particles(sharpy_batch* b, int e, double* theta, double* lnl, s
 /* Stage records of event e from the last run (HOST array of `cap` entries;
    *n = stages written). nuts_ms and reweight_ms are 0. Synchronous. */
 int sharpy_batch_stages(sharpy_batch* b, int e, sharpy_stage* stages, int cap, int* n);
-/* Slot count (particles per NUTS CTA: 8, 16 or 32) the batch's launches
+/* Slot count (particles per NUTS CTA: 4, 8, 16 or 32) the batch's launches
    use, picked by timing each candidate on full mutations of copies of the
    particles at the third stage round of the first run (0 until then; the
    launches use a count derived from the CTA count meanwhile). The results do
    not depend on it. */
 int sharpy_batch_slots(sharpy_batch* b);
-/* Set the slot count (8, 16 or 32) instead of tuning it; 0 tunes it again on
+/* Set the slot count (4, 8, 16 or 32) instead of tuning it; 0 tunes it again on
    the next run. SHARPY_EINVAL for other values. */
 int sharpy_batch_set_slots(sharpy_batch* b, int slots);
 /* Kernels the last sharpy_batch_run launched: eager launches counted as they

@@ -98,6 +98,7 @@ _SIGS = {
                                               C.c_int, C.c_int, C.c_uint64, C.c_uint64, C.c_int, _VP, _VP]),
     "sharpy_set_nuts_tick_limit": (C.c_int, [_CTX, C.c_int64]),
     "sharpy_set_stage_test_hooks": (C.c_int, [_CTX, C.c_int, C.c_int]),
+    "sharpy_set_nuts_slots": (C.c_int, [_CTX, C.c_int]),
     "sharpy_set_shard": (C.c_int, [_CTX, C.c_int64]),
     "sharpy_nuts_mutate_local": (C.c_int, [_CTX, C.c_int64, C.c_double, _VP, _VP, _VP, _VP, _VP, C.c_double,
                                            C.c_int, C.c_int, C.c_uint64, C.c_uint64, C.c_int, _VP, _VP]),

@@ -132,6 +132,10 @@ class Context:
         it does not apply), in later likelihood calls (0: tune)."""
         check(lib().sharpy_set_loglike_split(self._h, int(split)), "sharpy_set_loglike_split")
 
+    def set_nuts_slots(self, slots):
+        """Force 4, 8, 16 or 32 NUTS particle slots per CTA in later single-event launches (0: tuned/default)."""
+        check(lib().sharpy_set_nuts_slots(self._h, int(slots)), "sharpy_set_nuts_slots")
+
     def set_stage_test_hooks(self, skip_block=-1, wait_polls=0):
         """Failure-detection tests of the staged likelihood kernel: leave out the bulk copy of table block
         `skip_block` (-1: none) and poll each mbarrier wait at most `wait_polls` times (0: the default)."""

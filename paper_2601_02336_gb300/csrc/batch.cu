@@ -418,7 +418,7 @@ int sharpy_batch_slots(sharpy_batch* b) { return b ? b->slots : 0; }
 int64_t sharpy_batch_launches(sharpy_batch* b) { return b ? b->launches : -1; }
 
 int sharpy_batch_set_slots(sharpy_batch* b, int slots) {
-  if (!b || (slots != 0 && slots != 8 && slots != 16 && slots != 32)) return SHARPY_EINVAL;
+  if (!b || (slots != 0 && slots != 4 && slots != 8 && slots != 16 && slots != 32)) return SHARPY_EINVAL;
   b->slots = slots;
   return SHARPY_OK;
 }

@@ -62,6 +62,7 @@ struct sharpy_ctx {
   // likelihood kernel: warps per particle picked per call shape (loglike.cu)
   std::vector<LoglikeTuned> ll_tuned;
   int ll_split_forced = 0;  // > 0: every likelihood call uses this split (sharpy_set_loglike_split)
+  int nuts_slots_forced = 0;  // > 0: NUTS launches of this context use this slot count (sharpy_set_nuts_slots)
   int64_t tuned_n[3][2] = {{-1, -1}, {-1, -1}, {-1, -1}};
 };
 

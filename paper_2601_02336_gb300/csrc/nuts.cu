@@ -64,6 +64,7 @@ int enqueue_nuts(sharpy_ctx* c, int64_t n, const double* beta_ptr, double beta, 
   A.id_offset = c->first_id;
   A.stream_part = nullptr;
   const int lm = pminv ? 1 : 0;
+  if (!slots && c->nuts_slots_forced) slots = c->nuts_slots_forced;
   if (!slots && c->tuned_slots[precision][lm] && c->tuned_n[precision][lm] == n) slots = c->tuned_slots[precision][lm];
   if (!slots) {
     int dev = 0, sms = 0;
@@ -151,6 +152,14 @@ extern "C" int sharpy_set_nuts_tick_limit(sharpy_ctx* c, int64_t max_ticks) {
   if (rc) return rc;
   if (max_ticks < 0) return SHARPY_EINVAL;
   c->nuts_tick_limit = max_ticks;
+  return SHARPY_OK;
+}
+
+extern "C" int sharpy_set_nuts_slots(sharpy_ctx* c, int slots) {
+  int rc = check_ctx(c, false);
+  if (rc) return rc;
+  if (slots != 0 && slots != 4 && slots != 8 && slots != 16 && slots != 32) return SHARPY_EINVAL;
+  c->nuts_slots_forced = slots;
   return SHARPY_OK;
 }
 

@@ -202,7 +202,9 @@ template <int PREC, int NDET, int SLOTS>
 struct Nuts {
   using VT = typename std::conditional<PREC == SHARPY_FP64, double, float>::type;
   static constexpr int SPW = SLOTS / kNutsWarps;  // slots per warp
-  static constexpr int G = 32 / SPW;              // lanes per slot: 16, 8, 4
+  // lanes per slot: 16, 8, 4 (16 also for one slot per warp, whose group
+  // leaves the upper half-warp out: the group size fixes the arithmetic)
+  static constexpr int G = SPW == 1 ? 16 : 32 / SPW;
   static constexpr int DPL = kLaneDims / G;       // dimensions per lane: 1, 2, 4
   const NutsArgs& A;
   NutsShared<SLOTS, VT>& S;
@@ -661,7 +663,7 @@ struct NutsSmem {
 // which the 8- and 16-slot launches can use (9 % on 16384 particles); FP64:
 // two.
 template <int PREC, int NDET, int SLOTS>
-__global__ void __launch_bounds__(kNutsWarps * 32, PREC == SHARPY_FP64 ? 2 : 3)
+__global__ void __launch_bounds__(kNutsWarps * 32, PREC == SHARPY_FP64 ? 2 : (SLOTS == 4 ? 4 : 3))
     nuts_kernel(const __grid_constant__ NutsArgs P) {
   using DT = typename std::conditional<PREC == SHARPY_FP64, double, float>::type;
   using VT = DT;
@@ -767,10 +769,11 @@ __global__ void __launch_bounds__(kNutsWarps * 32, PREC == SHARPY_FP64 ? 2 : 3)
   using NT = Nuts<PREC, NDET, SLOTS>;
   constexpr int SPW = NT::SPW, G = NT::G, DPL = NT::DPL;
   static_assert(SLOTS % kNutsWarps == 0, "slots are shared evenly by the warps");
-  const int my = warp * SPW + lane / G;  // this lane's slot
+  const bool in_group = lane / G < SPW;   // false: the idle half-warp of a one-slot warp
+  const int my = in_group ? warp * SPW + lane / G : -1;  // this lane's slot
   const int tg = lane % G;                // its lane within the slot's group
   const unsigned gmask = (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << (lane - tg);
-  {
+  if (in_group) {
     Slot<VT> sl;
     NT nu(A, S, my, tg, gmask);
     sl.pid = (int64_t)s_block * SLOTS + my;
@@ -923,7 +926,7 @@ __global__ void __launch_bounds__(kNutsWarps * 32, PREC == SHARPY_FP64 ? 2 : 3)
     // machines, each on the lane group assigned to it this tick (the scalar
     // parts run identically on every lane of the group); which group runs a
     // slot does not change what it computes
-    const int cs = S.cslot[warp * SPW + lane / G];
+    const int cs = in_group ? S.cslot[warp * SPW + lane / G] : -1;
     if (cs >= 0) {
       if (gw && A.stream_part && sc[cs].ok && sc[cs].kisco >= kChunkBins) {
         // the slot's streams, in stream order (the sum sweep() forms on one warp)
@@ -974,6 +977,7 @@ __global__ void __launch_bounds__(kNutsWarps * 32, PREC == SHARPY_FP64 ? 2 : 3)
     __syncthreads();  // the control warp reads every slot's pending flag next
   }
   // write back
+  if (!in_group) return;
   const Slot<VT> sl = S.sstate[my];
   if (sl.pid < A.n) {
     NT nu(A, S, my, tg, gmask);
@@ -1015,6 +1019,7 @@ int launch_nuts_impl(int slots, const NutsArgs& A, unsigned grid, cudaStream_t s
     return cudaGetLastError() == cudaSuccess ? SHARPY_OK : SHARPY_ECUDA;
   };
   const bool local = A.local_metric != 0;
+  if (slots == 4) return go(nuts_kernel<P, ND, 4>, 4, nuts_smem_bytes<P, ND, 4>(local));
   if (slots == 32) return go(nuts_kernel<P, ND, 32>, 32, nuts_smem_bytes<P, ND, 32>(local));
   if (slots == 16) return go(nuts_kernel<P, ND, 16>, 16, nuts_smem_bytes<P, ND, 16>(local));
   return go(nuts_kernel<P, ND, 8>, 8, nuts_smem_bytes<P, ND, 8>(local));

@@ -81,7 +81,7 @@ extern "C" int sharpy_smc_run(sharpy_ctx* c, const sharpy_smc_options* o, uint64
   // run buffers: theta, grad [N][D], lnl [N], stats [N], scalars, cov, record;
   // copies of theta, grad, lnl for the autotuner's trials when it has to run
   const bool local = o->metric == 2;  // per-particle metric: [N][D][D] inverse and Cholesky factor
-  const bool tune = !(c->tuned_slots[o->precision][local] && c->tuned_n[o->precision][local] == n);
+  const bool tune = !c->nuts_slots_forced && !(c->tuned_slots[o->precision][local] && c->tuned_n[o->precision][local] == n);
   size_t bytes = (size_t)n * (2 * D + 1) * sizeof(double) * (tune ? 2 : 1) + (size_t)n * sizeof(sharpy_nuts_stats) +
                  (8 + D * D + kRec) * sizeof(double) + (local ? 2 * (size_t)n * D * D * sizeof(double) : 0);
   char* buf = nullptr;

@@ -17,8 +17,8 @@
 
 namespace sharpy {
 
-constexpr int kSlotChoices[] = {8, 16, 32};
-constexpr int kNumSlotChoices = 3;
+constexpr int kSlotChoices[] = {4, 8, 16, 32};
+constexpr int kNumSlotChoices = 4;
 // Warps that share one particle's sweep in the standalone likelihood kernel
 // (plus the staged kernel, choice 16, on long segments of the mixed path).
 constexpr int kSplitChoices[] = {1, 2, 4, 8};

@@ -46,7 +46,7 @@ def test_batch_matches_separate_runs(precision):
     kw = dict(alpha=0.5, n_mut=2, max_depth=6, metric=0, eps_scale=0.5, precision=precision, max_stages=200)
     b = api.Batch(ctxs, [w.n_particles for w in ws], **kw)
     res, rounds = b.run(keys)
-    assert b.slots in (0, 8, 16, 32)  # 0: every event finished before the tuning round
+    assert b.slots in (0, 4, 8, 16, 32)  # 0: every event finished before the tuning round
     assert rounds >= max(r["n_stages"] for r in res)
     _check_against_runs(b, ws, ctxs, keys, res, **kw)
     # a second run replays the cached graph without tuning and repeats itself
@@ -56,11 +56,12 @@ def test_batch_matches_separate_runs(precision):
     assert b.launches == 1 + 2 * len(ws) + 7 * rounds2
 
 
-@pytest.mark.parametrize("slots", [8, 32])
+@pytest.mark.parametrize("slots", [4, 8, 32])
 def test_batch_forced_slots_match_separate_runs(slots):
     """The batched NUTS launch with a forced slot count (32: many sweeps per CTA, each warp runs whole
-    particles; 8: few, the warps share each particle) against separate runs, bit for bit: a particle's
-    trajectory must not depend on how its CTA schedules the sweeps."""
+    particles; 8: few; 4: one sweep and one state machine per warp, on a 16-lane group with the upper half-warp
+    idle) against separate runs, bit for bit: a particle's trajectory must not depend on how its CTA schedules
+    the sweeps."""
     G.require_gpu()
     ws = _uneven_events()
     ctxs = [api.make_event(w, seed=10 + i)[0] for i, w in enumerate(ws)]

@@ -312,3 +312,33 @@ def test_nuts_long_signal_streams_match_oracle():
     assert np.max(np.abs(lm.cpu().numpy() - l.cpu().numpy())) <= 1e-6 * max(1.0, float(l.abs().max()))
     assert np.max(np.abs(l64.cpu().numpy() - l.cpu().numpy())) <= 1e-2
     assert ctx.status() == 0
+
+
+def test_nuts_slot_count_invariant():
+    """The slot count per CTA (sharpy_set_nuts_slots: 4, 8, 16, 32) changes how a CTA schedules its particles'
+    sweeps and state machines, never what a particle computes: positions, ln L, gradients and the transition
+    statistics are bit-identical, on the 11-D workload from prior draws at a small beta (deep trees, reflections at
+    the box) and near the injection."""
+    G.require_gpu()
+    w = inputs.bbh11()
+    ev, ctx, th_inj, _ = G.event_pair(w)
+    n = 300  # ragged last CTA for every slot count
+    th = np.vstack([inputs.prior_draws(w, n // 2, 31), inputs.ball(w, th_inj, n - n // 2, 32, rel=1e-3)])
+    t0 = G.to_dev(th)
+    l0, g0 = ctx.loglike_grad(t0, "mixed")
+    step = 0.5 * float(np.min(np.std(th, axis=0)))
+    ref = None
+    for slots in (8, 4, 16, 32):
+        ctx.set_nuts_slots(slots)
+        t, l, g = t0.clone(), l0.clone(), g0.clone()
+        st = api.Context.stats_to_numpy(ctx.nuts_mutate(0.01, t, l, g, None, step, 6, 2, key=41, ctr=3,
+                                                        precision="mixed"))
+        out = (t, l, g, st)
+        if ref is None:
+            ref = out
+            continue
+        assert torch.equal(t, ref[0]) and torch.equal(l, ref[1]) and torch.equal(g, ref[2]), slots
+        for f in ("accept_sum", "depth_sum", "n_leapfrog", "n_divergent", "active_bins"):
+            assert np.array_equal(st[f], ref[3][f]), (slots, f)
+    ctx.set_nuts_slots(0)
+    assert ctx.status() == 0
