@@ -29,9 +29,9 @@
  * Parity pins live in tests/ (closed forms, finite differences, analytic
  * evidences, brute force; the PN phase coefficients, sigma included, through
  * the chirp time against the published TaylorT2 series and an energy-balance
- * derivation). Parity unpinned: the constant phase terms (the "1" of
- * 1 + 3 ln(v / v_lso) and v_lso itself), which shift Psi by a constant that
- * phi_c absorbs; only the formula as written is checked.
+ * derivation; the constant phase terms, i.e. the "1" of 1 + 3 ln(v / v_lso)
+ * and v_lso, through Psi itself against the stationary-phase transform of the
+ * energy-balance orbit with its 2.5PN logarithm referenced at v_lso = 6^-1/2).
  */
 #ifndef SHARPY_ORACLE_H
 #define SHARPY_ORACLE_H

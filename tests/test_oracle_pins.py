@@ -85,8 +85,8 @@ def test_1pn_chirp_time_coefficient():
 # variables). The oracle's t(f) comes from its exact (dual-number) derivative of
 # Psi, using f dPsi/df = M_c dPsi/dM_c (Psi depends on f and M_c only through
 # v^3 ~ M_c f at fixed q). Constant phase terms (the "1" of the 2.5PN factor
-# 1 + 3 ln(v/v_lso), and v_lso) have no effect on t(f): they are degenerate with
-# phi_c.
+# 1 + 3 ln(v/v_lso), and v_lso) have no effect on t(f); the stationary-phase
+# test below pins them on Psi itself.
 
 def _oracle_chirp_time(mc, q, c1, c2, v):
     """t(f) - t_c of the oracle's phase at the frequency where v = (pi M T_sun f)^(1/3)."""
@@ -131,6 +131,13 @@ def _energy_balance_taus(q, c1, c2):
     so products of spin-orbit terms, which start at 3PN, are dropped); E and F here carry no
     spin-spin terms (those enter through sigma)."""
     sp = pytest.importorskip("sympy")
+    L, taus = _energy_balance_series(q, c1, c2)
+    return [sp.lambdify(L, t) for t in taus]
+
+
+def _energy_balance_series(q, c1, c2):
+    """(L, [tau_k(L)]) as exact sympy expressions; see _energy_balance_taus."""
+    sp = pytest.importorskip("sympy")
     R, pi, ge = sp.Rational, sp.pi, sp.EulerGamma
     L, s = sp.Symbol("L"), sp.Symbol("s")  # L = ln v; s marks each spin-orbit factor
     q, c1, c2 = R(q), R(c1), R(c2)
@@ -163,8 +170,8 @@ def _energy_balance_taus(q, c1, c2):
         a = sp.expand(a.coeff(s, 0) + (a.coeff(s, 1) if k <= 5 else 0))
         b, c, n = a.coeff(L, 0), a.coeff(L, 1), k - 8  # integrate v^(n-1) (b + c L)
         integral = b / n + c * (L - R(1, n)) / n
-        taus.append(sp.lambdify(L, sp.expand(integral * R(5, 32) / eta * R(-256, 5) * eta)))
-    return taus
+        taus.append(sp.expand(integral * R(5, 32) / eta * R(-256, 5) * eta))
+    return L, taus
 
 
 _PN_CASES = [(1.0, 0.0, 0.0), (0.25, 0.0, 0.0), (0.6, 1 / 3, -0.5), (0.125, 0.9, 0.7), (0.9, -0.8, 0.2)]
@@ -207,6 +214,50 @@ def test_chirp_time_energy_balance(q, c1, c2):
         ser = sum(float(taus[k](lv)) * v ** k for k in range(8)) - 2.0 * sigma * v ** 4
         t_pub = -5.0 * mtot * TSUN / (256.0 * eta * v ** 8) * ser
         assert abs(t_or / t_pub - 1.0) < 1e-12, (q, c1, c2, v, t_or, t_pub)
+
+
+@pytest.mark.parametrize("q,c1,c2", _PN_CASES)
+def test_phase_stationary_phase_of_energy_balance(q, c1, c2):
+    """The oracle's Psi itself, constant terms included, against the stationary-phase transform of
+    the energy-balance orbit: Psi(f) = 2 pi f (t - t_c) - 2 (phi - phi_c) at the frequency where the
+    GW frequency is twice the orbital one, with t(v) from the published E(x) and F(x) as above and
+    the orbital phase phi(v) integrated from d phi/dv = (v^3/M) dt/dv. Every term of phi is fixed by
+    the integration except the 2.5PN logarithm's reference, taken at the Schwarzschild
+    last-stable-orbit velocity v_lso = 6^(-1/2) (the TaylorF2 reading the oracle states). This pins
+    what the chirp-time tests cannot see: the "1" of the 2.5PN factor 1 + 3 ln(v/v_lso), the factor 3,
+    and v_lso, each an eta- and spin-dependent constant phase, to 1e-12 of the Newtonian term."""
+    sp = pytest.importorskip("sympy")
+    R = sp.Rational
+    L, taus = _energy_balance_series(q, c1, c2)
+    taus = list(taus)
+    taus[4] = taus[4] - 2 * R(_sigma_aligned(q, c1, c2))  # 2PN spin-spin, as in the chirp-time tests
+    x1, x2 = 1 / (1 + R(q)), R(q) / (1 + R(q))
+    eta = x1 * x2
+    v = sp.exp(L)
+    l_lso = -sp.log(6) / 2
+    # t - t_c = M T(v); phi - phi_c = -(5/(256 eta)) sum_k I_k(v)
+    T = -R(5, 256) / eta * sum(taus[k] * v ** (k - 8) for k in range(8))
+    phi = 0
+    for k in range(8):
+        a = sp.expand((k - 8) * taus[k] + sp.diff(taus[k], L))  # d/dv [tau_k v^(k-8)] = a v^(k-9)
+        b, c, m = a.coeff(L, 0), a.coeff(L, 1), k - 5            # integrate v^(m-1) (b + c L)
+        assert sp.expand(a - b - c * L) == 0
+        if m == 0:
+            assert c == 0
+            phi += b * (L - l_lso)
+        else:
+            phi += (b / m + c * (L - R(1, m)) / m) * v ** m
+    phi = -R(5, 256) / eta * phi
+    psi = sp.lambdify(L, 2 * v ** 3 * T - 2 * phi)
+    mc = 20.0
+    eta_f = float(eta)
+    mtot = mc * eta_f ** -0.6
+    for vv in np.linspace(0.05, 1.0, 40):
+        f = vv ** 3 / (math.pi * TSUN * mtot)
+        got = oracle.pn_phase(mc, q, c1, c2, f)
+        want = float(psi(math.log(vv)))
+        newton = 3.0 / (128.0 * eta_f * vv ** 5)
+        assert abs(got - want) < 1e-12 * newton, (q, c1, c2, vv, got, want)
 
 
 def test_spin_orbit_beta_identity():
