@@ -70,17 +70,19 @@ WORK = {p: work(p) for p in ("mixed", "split", "fp64")}
 # Each kernel's counts are keyed to the device-code files its instructions
 # come from (context.cuh, the host-side context, is not among them).
 COUNTED_SOURCES = {"nuts": ["nuts_kernel.cuh", "sweep.cuh", "physics.cuh", "common.cuh", "dfloat.cuh"],
-                   "loglike": ["loglike_kernel.cuh", "bulk.cuh", "sweep.cuh", "physics.cuh", "common.cuh", "dfloat.cuh"]}
-COUNTED = {"sources_sha256_16": {"nuts": "4c9bc0a722a82040", "loglike": "35e895237a35d5c7"},
+                   "loglike": ["loglike_kernel.cuh", "split_stage.cuh", "bulk.cuh", "sweep.cuh", "physics.cuh",
+                               "common.cuh", "dfloat.cuh"]}
+COUNTED = {"sources_sha256_16": {"nuts": "4c9bc0a722a82040", "loglike": "43066a7c70b78fc5"},
            "nuts": {"mixed": {"fp64": 2.9620, "fp32": 107.01},
                     "split": {"fp64": 0.2756, "fp32": 126.67},
                     "fp64": {"fp64": 110.50, "fp32": 0.0152}},
            # the likelihood kernels, one call each with the tuner's choice for
            # that shape: 2048 vectors of the 11-D workload (1 warp per vector),
-           # 8192 vectors of the 259585-bin segment (mixed: the staged kernel;
-           # FP64: 4 warps per vector)
+           # 8192 vectors of the 259585-bin segment (mixed and split: the staged
+           # kernel; FP64: 4 warps per vector)
            "loglike": {"bbh11": {"mixed": {"fp64": 2.8057, "fp32": 88.321}},
                        "bns": {"mixed": {"fp64": 2.6686, "fp32": 81.405},
+                               "split": {"fp64": 0.0019, "fp32": 101.07},
                                "fp64": {"fp64": 90.365, "fp32": 0.0}}},
            "traffic": {"mixed": 3830016, "split": 3913984, "fp64": 4599040},
            # the same captures: FP64 pipe busy, warps active and issue active

@@ -190,8 +190,9 @@ int sharpy_loglike_grad(sharpy_ctx* ctx, int64_t n, const double* theta, double*
    N vectors at `precision` (with_grad: with or without the gradient) on its
    current event's grid; 0 before the first such call. */
 int sharpy_loglike_split(sharpy_ctx* ctx, int64_t n, int precision, int with_grad);
-/* Use `split` (1, 2, 4 or 8 warps per vector, or 16: the staged kernel,
-   which falls back to 8 where it does not apply) in every later
+/* Use `split` (1, 2, 4 or 8 warps per vector, or 16: the staged kernel of
+   segments of at least 65536 bins on the mixed and split paths, which falls
+   back to 8 where it does not apply) in every later
    sharpy_loglike_grad call of the context instead of the tuned choice; 0
    returns to tuning. SHARPY_EINVAL for other values. */
 int sharpy_set_loglike_split(sharpy_ctx* ctx, int split);

@@ -128,8 +128,8 @@ class Context:
         return lib().sharpy_loglike_split(self._h, int(n), _prec(precision), 1 if grad else 0)
 
     def set_loglike_split(self, split):
-        """Force 1, 2, 4 or 8 warps per vector, or 16 (the staged kernel of long segments, mixed path; 8 where
-        it does not apply), in later likelihood calls (0: tune)."""
+        """Force 1, 2, 4 or 8 warps per vector, or 16 (the staged kernel of long segments, mixed and split
+        paths; 8 where it does not apply), in later likelihood calls (0: tune)."""
         check(lib().sharpy_set_loglike_split(self._h, int(split)), "sharpy_set_loglike_split")
 
     def set_nuts_slots(self, slots):

@@ -16,12 +16,13 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsharpy.so")
 # (source, extra nvcc flags, object tag): nuts_inst.cu is compiled once per
 # (precision, detector count) and loglike_inst.cu once per precision, so the
-# kernel variants build in parallel; loglike_staged.cu holds the staged
-# likelihood kernel.
+# kernel variants build in parallel; loglike_staged.cu and
+# loglike_staged_split.cu hold the staged likelihood kernel's two paths.
 UNITS = [("context.cu", [], "context"), ("loglike.cu", [], "loglike"), ("smc.cu", [], "smc"),
          ("nuts.cu", [], "nuts"), ("run.cu", [], "run"), ("probe.cu", [], "probe"),
          ("batch.cu", [], "batch"), ("recycle.cu", [], "recycle"),
-         ("metric.cu", [], "metric"), ("loglike_staged.cu", [], "loglike_staged")] + [
+         ("metric.cu", [], "metric"), ("loglike_staged.cu", [], "loglike_staged"),
+         ("loglike_staged_split.cu", [], "loglike_staged_split")] + [
     ("nuts_inst.cu", [f"-DSHARPY_NUTS_PREC={p}", f"-DSHARPY_NUTS_NDET={d}"], f"nuts_p{p}_{d}")
     for p in (0, 1, 2) for d in (1, 2, 3)] + [
     ("loglike_inst.cu", [f"-DSHARPY_LL_PREC={p}"], f"loglike_p{p}") for p in (0, 1, 2)]

@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "context.cuh"
+#include "split_stage.cuh"
 
 using namespace sharpy;
 
@@ -30,8 +31,10 @@ int check_ctx(sharpy_ctx* ctx, bool need_data) {
 }
 
 // One CTA per staged record: thread i copies bin g kStageBins + i of every
-// table the mixed sweep reads (zeros past the last bin).
-__global__ void stage_tables_kernel(DevEvent ev, unsigned char* out) {
+// table the mixed sweep reads into record g of the mixed set, and of every
+// table the split sweep reads into record g of the split set (zeros past the
+// last bin).
+__global__ void stage_tables_kernel(DevEvent ev, int nb, unsigned char* out) {
   const int g = blockIdx.x, i = threadIdx.x;
   const int64_t K = ev.n_bins, k = (int64_t)g * kStageBins + i;
   const bool in = k < K;
@@ -46,6 +49,15 @@ __global__ void stage_tables_kernel(DevEvent ev, unsigned char* out) {
   constexpr int b64_j[4] = {0, 1, 2, 4};
   for (int r = 0; r < 4; ++r) b64[r * kStageBins + i] = in ? ev.b64[b64_j[r] * K + k] : 0.0;
   for (int a = 0; a < ev.n_det; ++a) e32[a * kStageBins + i] = in ? ev.e32[a * K + k] : make_float2(0.0f, 0.0f);
+  unsigned char* srec = out + split_set_offset(nb, ev.n_det) + (size_t)g * split_rec_bytes(ev.n_det);
+  float* sb32 = reinterpret_cast<float*>(srec);
+  float* slo = reinterpret_cast<float*>(srec + split_off_lo());
+  float2* se32 = reinterpret_cast<float2*>(srec + split_off_e32());
+  for (int j = 0; j < kNBasis; ++j) {
+    sb32[j * kStageBins + i] = in ? ev.b32[j * K + k] : 0.0f;
+    slo[j * kStageBins + i] = in ? ev.b32lo[j * K + k] : 0.0f;
+  }
+  for (int a = 0; a < ev.n_det; ++a) se32[a * kStageBins + i] = in ? ev.e32[a * K + k] : make_float2(0.0f, 0.0f);
 }
 
 }  // namespace sharpy
@@ -305,12 +317,13 @@ int sharpy_set_data(sharpy_ctx* c, int n_det, int64_t n_bins, double f_min, doub
   // staged records of a long segment (rebuilt with every data set: they hold E)
   if (c->model.model == SHARPY_MODEL_TAYLORF2 && K >= kStageMinBins) {
     const int nb = (int)((K + kStageBins - 1) / kStageBins);
-    if (!c->d_stage && cudaMalloc(&c->d_stage, (size_t)nb * stage_rec_bytes(n_det)) != cudaSuccess) {
+    const size_t bytes = split_set_offset(nb, n_det) + (size_t)nb * split_rec_bytes(n_det);
+    if (!c->d_stage && cudaMalloc(&c->d_stage, bytes) != cudaSuccess) {
       c->d_stage = nullptr;
       free_event(c);
       return SHARPY_ENOMEM;
     }
-    stage_tables_kernel<<<nb, kStageBins>>>(ev, c->d_stage);
+    stage_tables_kernel<<<nb, kStageBins>>>(ev, nb, c->d_stage);
     if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
       free_event(c);
       return SHARPY_ECUDA;

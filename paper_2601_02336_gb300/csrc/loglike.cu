@@ -111,7 +111,7 @@ static int launch_ll(sharpy_ctx* c, int64_t n, const double* th, double* lnl, do
   TuneCandidate cands[kNumSplitChoices + 1];
   int nc = 0;
   for (int i = 0; i < kNumSplitChoices; ++i) cands[nc++].slots = kSplitChoices[i];
-  if (PREC == SHARPY_MIXED && c->ev.stage) cands[nc++].slots = kSplitStaged;
+  if (PREC != SHARPY_FP64 && c->ev.stage) cands[nc++].slots = kSplitStaged;
   auto trial = [&](int split, cudaStream_t ts) -> int {
     return launch_ll_prec<PREC, GRAD>(c, split, n, th, lnl, grad, ts) == cudaSuccess ? SHARPY_OK : SHARPY_ECUDA;
   };

@@ -6,6 +6,7 @@
 #pragma once
 #include "bulk.cuh"
 #include "context.cuh"
+#include "split_stage.cuh"
 #include "sweep.cuh"
 
 namespace sharpy {
@@ -109,8 +110,8 @@ loglike_kernel(DevModel m, DevEvent ev, int64_t n, const double* __restrict__ th
   }
 }
 
-// Staged variant for long segments on the mixed path (warps-per-vector
-// choice kSplitStaged): one vector per warp, kWarps vectors per CTA walking
+// Staged variant for long segments on the mixed and split paths
+// (warps-per-vector choice kSplitStaged): one vector per warp, kWarps vectors per CTA walking
 // the same bins in step. Each block of kStageBins bins of the tables comes
 // into shared memory by one bulk copy (two buffers, each completed on an
 // mbarrier) and is read there by all the CTA's vectors, instead of by each
@@ -118,7 +119,9 @@ loglike_kernel(DevModel m, DevEvent ev, int64_t n, const double* __restrict__ th
 // s: chunks s, s + kStreams, ...; the 8 blocks of a chunk in order), each
 // vector runs mixed_bin on the same bins in the same order and flushes at the
 // same chunk ends, and the streams are added in order in FP64: the moments
-// equal those of the other choices bit for bit.
+// equal those of the other choices bit for bit. The split path (SPLIT) reads
+// its own records (split_stage.cuh), which carry the lo parts of every basis
+// function instead of the FP64 tables.
 constexpr int kSplitStaged = 16;
 
 // The walk over the blocks for a CTA whose vectors' last active bin is kmax.
@@ -136,14 +139,16 @@ struct StageWalk {
   }
 };
 
-template <bool GRAD, int NDET>
+template <bool GRAD, int NDET, bool SPLIT>
 __global__ void __launch_bounds__(kWarps * 32, 2)
 loglike_staged_kernel(DevModel m, DevEvent ev, int64_t n, const double* __restrict__ theta, double* __restrict__ lnl,
                       double* __restrict__ grad, int* status, int skip_block, int wait_polls) {
   constexpr int NACC = MomCount<NDET, GRAD>::value;
   using FS = FlushShape<NACC>;
   constexpr int NOUT = FS::KEEP;
-  constexpr int REC = stage_rec_bytes(NDET);
+  constexpr int REC = SPLIT ? split_rec_bytes(NDET) : stage_rec_bytes(NDET);
+  using Ld = typename std::conditional<SPLIT, StagedSplitBin, StagedBin>::type;
+  const unsigned char* recs = ev.stage + (SPLIT ? split_set_offset(ev.stage_blocks, NDET) : 0);
   extern __shared__ __align__(128) unsigned char stage_buf[];  // two records
   __shared__ __align__(8) uint64_t full[2];
   __shared__ SweepCoef sc[kWarps];
@@ -158,7 +163,7 @@ loglike_staged_kernel(DevModel m, DevEvent ev, int64_t n, const double* __restri
     if (p < n) {
       double th[kMaxDim];
       for (int i = 0; i < D; ++i) th[i] = theta[p * D + i];
-      prologue<float, GRAD, false>(m, ev, th, sc[lane], ec[lane]);
+      prologue<float, GRAD, SPLIT>(m, ev, th, sc[lane], ec[lane]);
     } else {
       sc[lane].ok = 0;
       sc[lane].kisco = -1;
@@ -193,7 +198,7 @@ loglike_staged_kernel(DevModel m, DevEvent ev, int64_t n, const double* __restri
     for (int q = 0; q < 2 && issue.valid(); ++q, issue.next()) {
       if (issue.block() == skip_block) continue;
       mbar_arrive_expect_tx(&full[q], REC);
-      bulk_copy_g2s(stage_buf + q * REC, ev.stage + (size_t)issue.block() * REC, REC, &full[q]);
+      bulk_copy_g2s(stage_buf + q * REC, recs + (size_t)issue.block() * REC, REC, &full[q]);
       ++issued[q];
     }
   bool timed_out = false;
@@ -221,14 +226,14 @@ loglike_staged_kernel(DevModel m, DevEvent ev, int64_t n, const double* __restri
             const int k0 = c * kChunkBins + b * kStageBins + u * 32;
             if (k0 > kend) break;
             const int k = k0 + lane;
-            if (k <= kend) mixed_bin<GRAD, NDET, false>(sc[warp], P, StagedBin{rec, u * 32 + lane}, acc);
+            if (k <= kend) mixed_bin<GRAD, NDET, SPLIT>(sc[warp], P, Ld{rec, u * 32 + lane}, acc);
           }
         }
         __syncthreads();  // every warp is done with this buffer
         if (threadIdx.x == 0 && issue.valid() && !abort_s) {
           if (issue.block() != skip_block) {
             mbar_arrive_expect_tx(&full[buf], REC);
-            bulk_copy_g2s(stage_buf + buf * REC, ev.stage + (size_t)issue.block() * REC, REC, &full[buf]);
+            bulk_copy_g2s(stage_buf + buf * REC, recs + (size_t)issue.block() * REC, REC, &full[buf]);
             ++issued[buf];
           }
           issue.next();
@@ -275,22 +280,24 @@ loglike_staged_kernel(DevModel m, DevEvent ev, int64_t n, const double* __restri
   }
 }
 
-template <bool GRAD, int NDET>
+template <bool GRAD, int NDET, bool SPLIT>
 inline cudaError_t launch_ll_staged(sharpy_ctx* c, int64_t n, const double* th, double* lnl, double* grad,
                                     cudaStream_t s) {
-  constexpr int bytes = 2 * stage_rec_bytes(NDET);
-  const cudaError_t e =
-      cudaFuncSetAttribute(loglike_staged_kernel<GRAD, NDET>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  constexpr int bytes = 2 * (SPLIT ? split_rec_bytes(NDET) : stage_rec_bytes(NDET));
+  const cudaError_t e = cudaFuncSetAttribute(loglike_staged_kernel<GRAD, NDET, SPLIT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
-  loglike_staged_kernel<GRAD, NDET><<<(unsigned)((n + kWarps - 1) / kWarps), kWarps * 32, bytes, s>>>(
+  loglike_staged_kernel<GRAD, NDET, SPLIT><<<(unsigned)((n + kWarps - 1) / kWarps), kWarps * 32, bytes, s>>>(
       c->model, c->ev, n, th, lnl, grad, c->d_status, c->stage_skip_block,
       c->stage_wait_polls > 0 ? c->stage_wait_polls : kMbarWaitPolls);
   return cudaGetLastError();
 }
 
-// Defined in loglike_staged.cu (compiled as a unit of its own).
+// Defined in loglike_staged.cu and loglike_staged_split.cu (units of their own).
 cudaError_t launch_ll_staged_unit(sharpy_ctx* c, bool grad, int ndet, int64_t n, const double* th, double* lnl,
                                   double* g, cudaStream_t s);
+cudaError_t launch_ll_staged_split_unit(sharpy_ctx* c, bool grad, int ndet, int64_t n, const double* th, double* lnl,
+                                        double* g, cudaStream_t s);
 
 template <int PREC, bool GRAD, int NDET, int SPLIT>
 inline void launch_ll_one(sharpy_ctx* c, int64_t n, const double* th, double* lnl, double* grad, cudaStream_t s) {
@@ -306,7 +313,10 @@ inline cudaError_t launch_ll_split(sharpy_ctx* c, int split, int64_t n, const do
     if constexpr (PREC == SHARPY_MIXED) {
       if (c->ev.stage) return launch_ll_staged_unit(c, GRAD, NDET, n, th, lnl, grad, s);
     }
-    split = 8;  // no staged tables, or another precision: the 8-warp split
+    if constexpr (PREC == SHARPY_MIXED_SPLIT) {
+      if (c->ev.stage) return launch_ll_staged_split_unit(c, GRAD, NDET, n, th, lnl, grad, s);
+    }
+    split = 8;  // no staged tables, or the FP64 path: the 8-warp split
   }
   switch (split) {
     case 2: launch_ll_one<PREC, GRAD, NDET, 2>(c, n, th, lnl, grad, s); break;

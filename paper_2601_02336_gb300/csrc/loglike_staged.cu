@@ -8,10 +8,15 @@ namespace sharpy {
 cudaError_t launch_ll_staged_unit(sharpy_ctx* c, bool grad, int ndet, int64_t n, const double* th, double* lnl,
                                   double* g, cudaStream_t s) {
   switch (ndet) {
-    case 1: return grad ? launch_ll_staged<true, 1>(c, n, th, lnl, g, s) : launch_ll_staged<false, 1>(c, n, th, lnl, g, s);
-    case 2: return grad ? launch_ll_staged<true, 2>(c, n, th, lnl, g, s) : launch_ll_staged<false, 2>(c, n, th, lnl, g, s);
+    case 1:
+      return grad ? launch_ll_staged<true, 1, false>(c, n, th, lnl, g, s)
+                  : launch_ll_staged<false, 1, false>(c, n, th, lnl, g, s);
+    case 2:
+      return grad ? launch_ll_staged<true, 2, false>(c, n, th, lnl, g, s)
+                  : launch_ll_staged<false, 2, false>(c, n, th, lnl, g, s);
     default:
-      return grad ? launch_ll_staged<true, 3>(c, n, th, lnl, g, s) : launch_ll_staged<false, 3>(c, n, th, lnl, g, s);
+      return grad ? launch_ll_staged<true, 3, false>(c, n, th, lnl, g, s)
+                  : launch_ll_staged<false, 3, false>(c, n, th, lnl, g, s);
   }
 }
 

@@ -236,10 +236,11 @@ def test_autograd_backward_is_the_adjoint():
 def test_loglike_split_factor_invariant(wname):
     """The likelihood kernel cuts a vector's bins into chunks of 2048 dealt to 8 streams merged in a fixed
     order, so the number of warps sharing a vector (1, 2, 4, 8: the tuner's choice) does not change ln L or
-    the gradient, bit for bit, on every path; nor does choice 16, the staged kernel (one vector per warp, the
-    tables of each 256-bin block brought into shared memory by one bulk copy), which the 259585-bin segment's
-    mixed path has and the others replace by 8. On that segment the streams' merge stays within the
-    long-signal tolerance of the oracle. The tuner's pick is one of the candidates."""
+    the gradient, bit for bit, on every path, with and without the gradient; nor does choice 16, the staged
+    kernel (one vector per warp, the tables of each 256-bin block brought into shared memory by one bulk copy),
+    which the 259585-bin segment's mixed and split paths have (each with records of its own) and the others
+    replace by 8. On that segment the streams' merge stays within the long-signal tolerance of the oracle. The
+    tuner's pick is one of the candidates."""
     G.require_gpu()
     w = getattr(inputs, wname)()
     ev, ctx, th_inj, _ = G.event_pair(w)
@@ -251,16 +252,19 @@ def test_loglike_split_factor_invariant(wname):
         for split in (1, 2, 4, 8, 16):
             ctx.set_loglike_split(split)
             l, g = ctx.loglike_grad(t, prec)
+            l0, _ = ctx.loglike_grad(t, prec, grad=False)
             if ref is None:
-                ref = (l, g)
+                ref = (l, g, l0)
             else:
                 assert torch.equal(l, ref[0]) and torch.equal(g, ref[1]), (prec, split)
-        if wname == "bns" and prec == "mixed":
+                assert torch.equal(l0, ref[2]), (prec, split, "no gradient")
+        if wname == "bns" and prec != "fp64":
             lref = oracle.loglike(helpers.oracle_model(w), ev, th[:4], grad=False)
-            assert np.max(np.abs(ref[0].cpu().numpy()[:4] - lref)) <= 1e-2
+            assert np.max(np.abs(ref[0].cpu().numpy()[:4] - lref)) <= 1e-2, prec
     ctx.set_loglike_split(0)
-    ctx.loglike_grad(t, "mixed")
-    assert ctx.loglike_split(n, "mixed") in ((1, 2, 4, 8, 16) if wname == "bns" else (1, 2, 4, 8))
+    for prec in ("mixed", "split"):
+        ctx.loglike_grad(t, prec)
+        assert ctx.loglike_split(n, prec) in ((1, 2, 4, 8, 16) if wname == "bns" else (1, 2, 4, 8)), prec
     assert ctx.status() == 0
 
 
