@@ -379,7 +379,7 @@ def _extra_workloads(args, flush):
     row = {"workload": "bns: 259585 bins x 3 detectors, 8192 vectors near the injection (sigma 1e-3 of the "
                        "prior width), one sharpy_loglike_grad call = ln L + gradient of all 8192",
            "active_bin_det_per_eval": float(_active_bins(w, th.cpu().numpy()).mean())}
-    for prec in ("mixed", "fp64"):
+    for prec in ("mixed", "split", "fp64"):
         ctx.loglike_grad(th, prec)  # the first call of this shape tunes the warps per vector
         _, ms = timed(lambda: ctx.loglike_grad(th, prec))
         row[prec] = {"ms_per_call": ms, "evals_per_s": 8192 / (ms * 1e-3),
