@@ -403,20 +403,25 @@ def _extra_workloads(args, flush):
 
 
 def main_nuts_launch(args):
-    """One persistent NUTS launch on fixed ensembles of the bbh11 event (2048 particles, depth 6, two
-    transitions, identity metric, step 0.5 x the ensemble's smallest standard deviation): "first" = prior
+    """One persistent NUTS launch on fixed ensembles of an event (by default bbh11: 2048 particles, depth 6,
+    two transitions, identity metric, step 0.5 x the ensemble's smallest standard deviation): "first" = prior
     draws at beta = 1e-4 (the first stage's regime: most trees reach the depth limit), "late" = a Gaussian
     ball around the injection (sigma 1e-3 of the prior width) at beta = 1 (a posterior-like stage). The
     launches are deterministic, so versions of the kernel are compared on identical work; also the command
-    the instruction-count and DRAM captures of the roofline are taken on (--ensemble picks one)."""
+    the instruction-count and DRAM captures of the roofline are taken on (--ensemble picks one; --workload,
+    --particles and --depth change the event, the ensemble size and the tree depth)."""
     import torch
 
     from paper_2601_02336_gb300 import api, inputs
     torch.cuda.set_device(0)
-    w = inputs.bbh11()
+    if args.workload not in inputs.WORKLOADS:
+        raise SystemExit("nuts_launch runs one event")
+    w = inputs.WORKLOADS[args.workload]()
+    n = args.particles or w.n_particles
+    depth = args.depth or w.max_depth
     ctx, th_inj, _ = api.make_event(w, seed=0)
-    sets = {"first": (inputs.prior_draws(w, w.n_particles, 1), 1e-4),
-            "late": (inputs.ball(w, th_inj, w.n_particles, 2, rel=1e-3), 1.0)}
+    sets = {"first": (inputs.prior_draws(w, n, 1), 1e-4),
+            "late": (inputs.ball(w, th_inj, n, 2, rel=1e-3), 1.0)}
     names = [args.ensemble] if args.ensemble else list(sets)
     if args.slots:
         ctx.set_nuts_slots(args.slots)
@@ -432,7 +437,7 @@ def main_nuts_launch(args):
             t, l, g = t0.clone(), l0.clone(), g0.clone()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            s = ctx.nuts_mutate(beta, t, l, g, None, eps, w.max_depth, w.n_mut, key=77, ctr=256,
+            s = ctx.nuts_mutate(beta, t, l, g, None, eps, depth, w.n_mut, key=77, ctr=256,
                                 precision=args.precision)
             e1.record(stream)
             torch.cuda.synchronize()
@@ -580,7 +585,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="bbh11", choices=["tiny", "bbh11", "bbh11_long", "bns", "batch64"])
     ap.add_argument("--mode", default="smc", choices=["smc", "loglike", "nuts_launch", "loglike_launch"])
-    ap.add_argument("--particles", type=int, default=0, help="loglike_launch: vectors per call (0: the workload's)")
+    ap.add_argument("--particles", type=int, default=0,
+                    help="loglike_launch and nuts_launch: vectors per call (0: the workload's)")
+    ap.add_argument("--depth", type=int, default=0, help="nuts_launch: NUTS tree depth (0: the workload's)")
     ap.add_argument("--split", type=int, default=0, choices=[0, 1, 2, 4, 8, 16],
                     help="loglike_launch: warps per vector, 16 = the staged kernel (0: tuned)")
     ap.add_argument("--ensemble", default=None, choices=["first", "late"], help="nuts_launch: one ensemble only")
