@@ -729,11 +729,19 @@ def main():
                  "dlnz": float(np.mean(lz_m) - np.mean(lz_o)),
                  "two_sigma": float(2.0 * math.sqrt(se_m ** 2 + se_f ** 2))}
         gold = os.path.join(ROOT, "tests", "golden", f"lnz_{w.name}_oracle.json")
-        if os.path.exists(gold) and world == 1:
-            # ln Z of the oracle's own full runs on this event (stored by tests/golden/make_lnz_oracle.py; the
-            # same injection and noise, its waveform from the oracle instead of the library: ~1e-12 apart)
+        gold_cfg = None
+        if os.path.exists(gold):
             with open(gold) as fh:
-                ref = [r["lnz"] for r in json.load(fh)["runs"]]
+                gold_cfg = json.load(fh)
+        same_sampler = gold_cfg is not None and all(
+            gold_cfg.get(k) == v for k, v in (("metric", w.metric), ("n_particles", w.n_particles),
+                                              ("max_depth", w.max_depth), ("n_mut", w.n_mut), ("alpha", w.alpha),
+                                              ("eps_scale", w.eps_scale)))
+        if same_sampler and world == 1:
+            # ln Z of the oracle's own full runs on this event with the same sampler settings (stored by
+            # tests/golden/make_lnz_oracle.py; the same injection and noise, its waveform from the oracle instead
+            # of the library: ~1e-12 apart)
+            ref = [r["lnz"] for r in gold_cfg["runs"]]
             se_r = np.std(ref, ddof=1) / math.sqrt(len(ref))
             other["vs_oracle"] = {
                 "oracle_runs": len(ref), "oracle_mean": float(np.mean(ref)),
