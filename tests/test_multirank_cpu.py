@@ -95,10 +95,13 @@ def _sharded_run(shards_per_rank):
     w = inputs.tiny()
     ev, _, _ = helpers.make_event(w, seed=0)
     model = helpers.oracle_model(w)
-    oracle.set_threads(1)
-    run = multirank.ShardedSMC(OracleShardBackend(model, ev), N_SHARD, w.alpha, w.n_mut, 4, w.metric,
-                               w.eps_scale, KEY_SHARD, shards_per_rank=shards_per_rank)
-    lnz = run.run()
+    prev = oracle.set_threads(1)  # restored below: later tests in this process use all cores
+    try:
+        run = multirank.ShardedSMC(OracleShardBackend(model, ev), N_SHARD, w.alpha, w.n_mut, 4, w.metric,
+                                   w.eps_scale, KEY_SHARD, shards_per_rank=shards_per_rank)
+        lnz = run.run()
+    finally:
+        oracle.set_threads(prev)
     recs = [(r["beta"], r["dlnz"], r["lnz"], np.asarray(r["ancestors"]).tolist()) for r in run.records]
     parts = [(lo, th.tolist(), lnl.tolist()) for lo, th, lnl, _ in run.state()]
     return lnz, recs, parts
