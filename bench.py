@@ -153,17 +153,28 @@ class ClockSampler:
         self.device = device
         self.proc = None
         self.lines = []
+        self.first = 0
 
     def start(self):
+        """Start sampling every 50 ms; returns once the first sample is in (at most 3 s), so that the timed
+        region that follows is sampled from its start."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except (OSError, ValueError):
             self.proc = None
+            return
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 3.0 and self.proc.poll() is None:
+            time.sleep(0.01)
+
+    def mark(self):
+        """The timed region starts: later samples are the ones reported (earlier ones only if none came)."""
+        self.first = len(self.lines)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -179,7 +190,8 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines[self.first:] or self.lines[-1:]
+        for ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 7:
                 continue
@@ -522,6 +534,7 @@ def main_batch(args):
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
+    clocks.mark()
     evals, bins, rounds, step_ms, lnzs, launches = 0.0, 0.0, [], [], [], 0
     for k in range(args.steps):
         flush.zero_()
@@ -571,7 +584,7 @@ def main_batch(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sharpy", choices=["sharpy", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "split", "fp64"])
@@ -645,6 +658,7 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
+    clocks.mark()
     evals = 0
     bins = 0.0
     nuts_ms = 0.0
