@@ -411,6 +411,24 @@ def _extra_workloads(args, flush):
                           "evals_per_s": sum(r["n_leapfrog"] for r in res) / (ms * 1e-3), "rounds": rounds,
                           "slots": b.slots}
     b.close()
+    del ctxs, b
+    # the timed workload's event, 8 independent runs (keys) through the batched driver: in a single run most
+    # stages' NUTS launches last as long as their slowest particle's trees, while batched the runs' tails overlap
+    w = inputs.bbh11()
+    R = 8
+    ctxs = [api.make_event(w, seed=0)[0] for _ in range(R)]
+    b = api.Batch(ctxs, [w.n_particles] * R, w.alpha, w.n_mut, w.max_depth, w.metric, w.eps_scale,
+                  precision="mixed", max_stages=500)
+    b.run([70_000 + e for e in range(R)])
+    (res, rounds), ms = timed(lambda: b.run([80_000 + e for e in range(R)]))
+    lz = [r["lnz"] for r in res]
+    out["bbh11_runs_batched"] = {"workload": f"{R} independent runs of the timed workload's event (same data, "
+                                             "keys differ) in one batched driver, mixed precision",
+                                 "ms_per_batch": ms, "ms_per_run_equivalent": ms / R,
+                                 "evals_per_s": sum(r["n_leapfrog"] for r in res) / (ms * 1e-3),
+                                 "rounds": rounds, "slots": b.slots, "lnz_mean": float(np.mean(lz)),
+                                 "lnz_sd": float(np.std(lz, ddof=1))}
+    b.close()
     return out
 
 
