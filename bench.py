@@ -623,7 +623,7 @@ def main():
                     help="loglike_launch: warps per vector, 16 = the staged kernel (0: tuned)")
     ap.add_argument("--ensemble", default=None, choices=["first", "late"], help="nuts_launch: one ensemble only")
     ap.add_argument("--slots", type=int, default=0, choices=[0, 4, 8, 16, 32],
-                    help="batch64 and nuts_launch: NUTS particles per CTA (0: autotuned / default)")
+                    help="NUTS particles per CTA (0: autotuned / default)")
     ap.add_argument("--metric", type=int, default=None, choices=[0, 1, 2],
                     help="NUTS metric (default: the workload's): 0 identity, 1 covariance, 2 per-particle local")
     args = ap.parse_args()
@@ -664,6 +664,8 @@ def main():
     if args.metric is not None:
         w.metric = args.metric
     ctx, th_inj, data = api.make_event(w, seed=multirank.event_seed(rank), device=local)
+    if args.slots:
+        ctx.set_nuts_slots(args.slots)
     run_args = (w.n_particles, w.alpha, w.n_mut, w.max_depth, w.metric, w.eps_scale)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
