@@ -104,6 +104,10 @@ _SIGS = {
                                         _P(NutsStats)]),
     "ref_fisher": (C.c_int, [_P(Model), _P(Event), C.c_int64, _D, _D]),
     "ref_local_metric": (C.c_int, [_P(Model), _P(Event), C.c_int64, _D, C.c_double, _D]),
+    "ref_local_inv_mass": (C.c_int, [_P(Model), _P(Event), C.c_int64, _D, C.c_double, _D]),
+    "ref_nuts_mutate_local_ids": (C.c_int, [_P(Model), _P(Event), C.c_int64, _P(C.c_int64), C.c_double, _D, _D,
+                                            _D, _D, C.c_double, C.c_int, C.c_int, C.c_uint64, C.c_uint32,
+                                            _P(NutsStats)]),
     "ref_recycle_weights": (C.c_int, [C.c_int64, C.c_int, _D, _D, _D, _D]),
     "ref_rejection_sample": (C.c_int, [C.c_int64, _D, C.c_uint64, _P(C.c_int32)]),
     "ref_prior_sample": (C.c_int, [_P(Model), C.c_int64, _D, C.c_uint64, C.c_uint32]),
@@ -310,8 +314,9 @@ def nuts_mutate(model, event, beta, theta, lnl, grad, inv_mass, step, max_depth,
     return theta, lnl, grad, stats
 
 
-def nuts_mutate_local(model, event, beta, theta, lnl, grad, inv_mass, step, max_depth, n_steps, key, ctr):
-    """nuts_mutate with one inverse mass matrix per particle (inv_mass [N][D][D])."""
+def nuts_mutate_local(model, event, beta, theta, lnl, grad, inv_mass, step, max_depth, n_steps, key, ctr,
+                      ids=None):
+    """nuts_mutate with one inverse mass matrix per particle (inv_mass [N][D][D]); ids as in nuts_mutate."""
     theta = _f64(theta).copy()
     lnl = _f64(lnl).copy()
     grad = _f64(grad).copy()
@@ -319,8 +324,15 @@ def nuts_mutate_local(model, event, beta, theta, lnl, grad, inv_mass, step, max_
     st = (NutsStats * n)()
     im = _f64(inv_mass)
     evp = C.byref(event.ev) if event is not None else None
-    _check(lib().ref_nuts_mutate_local(C.byref(model), evp, n, beta, _dp(theta), _dp(lnl), _dp(grad),
-                                       _dp(im), step, max_depth, n_steps, key, ctr, st), "nuts_mutate_local")
+    if ids is None:
+        _check(lib().ref_nuts_mutate_local(C.byref(model), evp, n, beta, _dp(theta), _dp(lnl), _dp(grad),
+                                           _dp(im), step, max_depth, n_steps, key, ctr, st), "nuts_mutate_local")
+    else:
+        idv = np.ascontiguousarray(ids, dtype=np.int64)
+        assert idv.shape == (n,)
+        _check(lib().ref_nuts_mutate_local_ids(C.byref(model), evp, n, idv.ctypes.data_as(C.POINTER(C.c_int64)),
+                                               beta, _dp(theta), _dp(lnl), _dp(grad), _dp(im), step, max_depth,
+                                               n_steps, key, ctr, st), "nuts_mutate_local")
     stats = {
         "accept_sum": np.array([s.accept_sum for s in st]),
         "depth_sum": np.array([s.depth_sum for s in st]),
@@ -399,6 +411,16 @@ def fisher(model, event, theta):
     n, d = theta.shape
     out = np.zeros((n, d, d))
     _check(lib().ref_fisher(C.byref(model), C.byref(event.ev), n, _dp(theta), _dp(out)), "fisher")
+    return out
+
+
+def local_inv_mass(model, event, theta, beta):
+    """The inverse mass matrices [N][D][D] smc_run's metric 2 mutates with at beta."""
+    theta = _f64(np.atleast_2d(theta))
+    n, d = theta.shape
+    out = np.zeros((n, d, d))
+    evp = C.byref(event.ev) if event is not None else None
+    _check(lib().ref_local_inv_mass(C.byref(model), evp, n, _dp(theta), beta, _dp(out)), "local_inv_mass")
     return out
 
 

@@ -194,6 +194,16 @@ int ref_nuts_mutate_local(const ref_model* m, const ref_event* ev, int64_t n, do
                           double* theta, double* lnl, double* grad, const double* inv_mass,
                           double step, int max_depth, int n_steps, uint64_t key, uint32_t ctr,
                           ref_nuts_stats* stats);
+/* The same on n rows of an ensemble, row i being particle ids[i] (as in
+   ref_nuts_mutate_ids). */
+int ref_nuts_mutate_local_ids(const ref_model* m, const ref_event* ev, int64_t n, const int64_t* ids,
+                              double beta, double* theta, double* lnl, double* grad, const double* inv_mass,
+                              double step, int max_depth, int n_steps, uint64_t key, uint32_t ctr,
+                              ref_nuts_stats* stats);
+/* The inverse mass matrices [N][D][D] of ref_smc_run's metric 2 at beta: each
+   particle's ref_local_metric, inverted through its Cholesky factor. */
+int ref_local_inv_mass(const ref_model* m, const ref_event* ev, int64_t n, const double* theta, double beta,
+                       double* inv_mass);
 
 /* Adaptive tempering step: beta_next, the incremental weights W (max 1),
    their ESS and the evidence increment dlnz = logsumexp(dbeta lnL) - ln N. */

@@ -295,12 +295,16 @@ int ref_nuts_mutate(const ref_model* m, const ref_event* ev, int64_t n, double b
                              ctr, stats);
 }
 
-// As ref_nuts_mutate, each particle with its own inverse mass matrix
+// As ref_nuts_mutate_ids, each particle with its own inverse mass matrix
 // (inv_mass [N][D][D]): the local metric of Sec. 5, fixed through the call.
-int ref_nuts_mutate_local(const ref_model* m, const ref_event* ev, int64_t n, double beta, double* theta,
-                          double* lnl, double* grad, const double* inv_mass, double step, int max_depth,
-                          int n_steps, uint64_t key, uint32_t ctr, ref_nuts_stats* stats) {
+int ref_nuts_mutate_local_ids(const ref_model* m, const ref_event* ev, int64_t n, const int64_t* ids,
+                              double beta, double* theta, double* lnl, double* grad, const double* inv_mass,
+                              double step, int max_depth, int n_steps, uint64_t key, uint32_t ctr,
+                              ref_nuts_stats* stats) {
   if (max_depth < 0 || max_depth > kMaxDepth || !inv_mass) return -1;
+  if (ids)
+    for (int64_t i = 0; i < n; ++i)
+      if (ids[i] < 0 || ids[i] > 0xffffffffLL) return -1;
   Sampler s;
   s.m = m;
   s.ev = ev;
@@ -315,8 +319,9 @@ int ref_nuts_mutate_local(const ref_model* m, const ref_event* ev, int64_t n, do
     for (int j = 0; j < D; ++j) cur.th[j] = theta[i * D + j];
     sp.evaluate(cur);
     ref_nuts_stats st = {0.0, 0, 0, 0};
+    const uint32_t pid = (uint32_t)(ids ? ids[i] : i);
     for (int t = 0; t < n_steps; ++t)
-      sp.transition(cur, key, (uint32_t)i, ctr + (uint32_t)t, step, max_depth, &st);
+      sp.transition(cur, key, pid, ctr + (uint32_t)t, step, max_depth, &st);
     for (int j = 0; j < D; ++j) {
       theta[i * D + j] = cur.th[j];
       grad[i * D + j] = cur.gl[j];
@@ -325,6 +330,13 @@ int ref_nuts_mutate_local(const ref_model* m, const ref_event* ev, int64_t n, do
     if (stats) stats[i] = st;
   }
   return 0;
+}
+
+int ref_nuts_mutate_local(const ref_model* m, const ref_event* ev, int64_t n, double beta, double* theta,
+                          double* lnl, double* grad, const double* inv_mass, double step, int max_depth,
+                          int n_steps, uint64_t key, uint32_t ctr, ref_nuts_stats* stats) {
+  return ref_nuts_mutate_local_ids(m, ev, n, nullptr, beta, theta, lnl, grad, inv_mass, step, max_depth, n_steps,
+                                   key, ctr, stats);
 }
 
 // Inverse of a symmetric positive-definite matrix through its Cholesky
@@ -540,6 +552,17 @@ int ref_smc_run(const ref_model* m, const ref_event* ev, const ref_smc_opts* o, 
   if (theta_out) std::memcpy(theta_out, th.data(), sizeof(double) * n * D);
   if (lnl_out) std::memcpy(lnl_out, l.data(), sizeof(double) * n);
   return beta >= 1.0 ? 0 : 1;
+}
+
+// The inverse mass matrices ref_smc_run's metric 2 mutates with: the local
+// metric of each particle at beta, each inverted by spd_inverse.
+int ref_local_inv_mass(const ref_model* m, const ref_event* ev, int64_t n, const double* theta, double beta,
+                       double* inv_mass) {
+  const int rc = ref_local_metric(m, ev, n, theta, beta, inv_mass);
+  if (rc) return rc;
+  const int D = m->n_dim;
+  for (int64_t i = 0; i < n; ++i) spd_inverse(D, inv_mass + i * D * D);
+  return 0;
 }
 
 }  // extern "C"

@@ -136,8 +136,13 @@ class GpuShardBackend:
         elif metric == 1:
             self.ctx.nuts_mutate(beta, th, lnl, grad, cov, eps_scale, max_depth, n_mut, key, ctr,
                                  precision=self.precision, stats=False)
+        elif metric == 2:
+            # each row's local metric at the new temperature (Sec. 5) needs only the row: no exchange
+            m = self.ctx.local_metric(th, beta, want=("inv_mass", "chol"))
+            self.ctx.nuts_mutate_local(beta, th, lnl, grad, m["inv_mass"], m["chol"], eps_scale, max_depth, n_mut,
+                                       key, ctr, precision=self.precision, stats=False)
         else:
-            raise ValueError("sharded runs support the identity (0) and covariance (1) metrics")
+            raise ValueError("metric must be 0 (identity), 1 (covariance) or 2 (local)")
         return th, lnl, grad
 
     def finish(self):

@@ -57,12 +57,18 @@ class OracleShardBackend:
 
     def mutate(self, first, state, beta, cov, metric, eps_scale, max_depth, n_mut, key, ctr):
         th, lnl, grad = state
+        ids = first + np.arange(th.shape[0], dtype=np.int64)
+        if metric == 2:
+            # each row's local metric at the new temperature (Sec. 5): needs only the row itself
+            minv = oracle.local_inv_mass(self.model, self.event, th, beta)
+            th, lnl, grad, _ = oracle.nuts_mutate_local(self.model, self.event, beta, th, lnl, grad, minv, eps_scale,
+                                                        max_depth, n_mut, key, ctr, ids=ids)
+            return th, lnl, grad
         if metric == 0:
             eps = eps_scale * min(math.sqrt(cov[j, j]) for j in range(cov.shape[0]))
             minv = None
         else:
             eps, minv = eps_scale, cov
-        ids = first + np.arange(th.shape[0], dtype=np.int64)
         th, lnl, grad, _ = oracle.nuts_mutate(self.model, self.event, beta, th, lnl, grad, minv, eps, max_depth,
                                               n_mut, key, ctr, ids=ids)
         return th, lnl, grad

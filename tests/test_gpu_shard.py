@@ -17,7 +17,8 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("wname,metric,precision", [("tiny", 0, "fp64"), ("tiny", 1, "mixed"),
-                                                     ("bbh11", 0, "mixed")])
+                                                     ("bbh11", 0, "mixed"), ("tiny", 2, "fp64"),
+                                                     ("bbh11", 2, "mixed")])
 def test_sharded_run_equals_single_run(wname, metric, precision):
     G.require_gpu()
     w = getattr(inputs, wname)(n_particles=1000) if wname == "bbh11" else inputs.tiny()

@@ -87,7 +87,7 @@ def test_single_rank_identity():
 N_SHARD, KEY_SHARD = 96, 4242
 
 
-def _sharded_run(shards_per_rank):
+def _sharded_run(shards_per_rank, metric=None):
     import oracle
     from paper_2601_02336_gb300 import inputs, multirank
     from tests import helpers
@@ -97,8 +97,9 @@ def _sharded_run(shards_per_rank):
     model = helpers.oracle_model(w)
     prev = oracle.set_threads(1)  # restored below: later tests in this process use all cores
     try:
-        run = multirank.ShardedSMC(OracleShardBackend(model, ev), N_SHARD, w.alpha, w.n_mut, 4, w.metric,
-                                   w.eps_scale, KEY_SHARD, shards_per_rank=shards_per_rank)
+        run = multirank.ShardedSMC(OracleShardBackend(model, ev), N_SHARD, w.alpha, w.n_mut, 4,
+                                   w.metric if metric is None else metric, w.eps_scale, KEY_SHARD,
+                                   shards_per_rank=shards_per_rank)
         lnz = run.run()
     finally:
         oracle.set_threads(prev)
@@ -147,3 +148,27 @@ def test_particle_sharding_bit_identical():
     assert lnz_o == lnz1
     assert [r["beta"] for r in rec_o] == [r[0] for r in rec1]
     assert np.array_equal(th_o, th1) and np.array_equal(l_o, l1)
+
+
+def test_particle_sharding_local_metric():
+    """The per-particle local metric (metric 2, Sec. 5) in the sharded driver: each shard forms its own rows'
+    metrics at the new temperature, so three shards on one rank give the one-shard run bit for bit, and that is
+    the oracle's own SMC run with metric 2."""
+    import oracle
+    from paper_2601_02336_gb300 import inputs
+    from tests import helpers
+    lnz1, rec1, parts1 = _sharded_run(1, metric=2)
+    lnz3, rec3, parts3 = _sharded_run(3, metric=2)
+    th1, l1 = _assemble([parts1])
+    th3, l3 = _assemble([parts3])
+    assert lnz3 == lnz1 and rec3 == rec1
+    assert np.array_equal(th3, th1) and np.array_equal(l3, l1)
+    assert len(rec1) >= 2
+    w = inputs.tiny()
+    ev, _, _ = helpers.make_event(w, seed=0)
+    lnz_o, th_o, l_o, rec_o = oracle.smc_run(helpers.oracle_model(w), ev, N_SHARD, w.alpha, w.n_mut, 4, 2,
+                                             w.eps_scale, key=KEY_SHARD)
+    assert lnz_o == lnz1
+    assert [r["beta"] for r in rec_o] == [r[0] for r in rec1]
+    assert np.array_equal(th_o, th1) and np.array_equal(l_o, l1)
+
