@@ -268,6 +268,30 @@ def test_loglike_split_factor_invariant(wname):
     assert ctx.status() == 0
 
 
+@pytest.mark.parametrize("n_bins", [65535, 65536, 65537, 65536 + 255, 65536 + 2048 * 8 + 1])
+def test_staged_kernel_segment_edges(n_bins):
+    """The staged kernel at the edges of its domain: segments one bin short of the staging threshold (choice 16
+    falls back to 8 warps), exactly at it, one bin and one record past it, and one bin into a stream's second
+    chunk. On the mixed and split paths, with and without the gradient, choice 16 gives choice 1's ln L and
+    gradient bit for bit, on 9 vectors (a full CTA of 8 and one more)."""
+    import dataclasses
+    G.require_gpu()
+    w = dataclasses.replace(inputs.bns(n_particles=9), n_bins=n_bins, f_min=20.0, df=1.0 / 64.0)
+    ctx, th_inj, _ = api.make_event(w, seed=0)
+    t = G.to_dev(np.vstack([inputs.prior_draws(w, 4, 6), inputs.ball(w, th_inj, 5, 7)]))
+    for prec in ("mixed", "split"):
+        for grad in (True, False):
+            ctx.set_loglike_split(1)
+            l1, g1 = ctx.loglike_grad(t, prec, grad=grad)
+            ctx.set_loglike_split(16)
+            l16, g16 = ctx.loglike_grad(t, prec, grad=grad)
+            assert torch.equal(l1, l16), (prec, grad)
+            if grad:
+                assert torch.equal(g1, g16), prec
+    ctx.set_loglike_split(0)
+    assert ctx.status() == 0
+
+
 def test_staged_kernel_wait_timeout_reports_status():
     """Failure detection without a fault in the staged kernel (choice 16). The test hook leaves out the bulk copy of
     one table block, so the mbarrier waits for it run out after a short poll bound. The call returns; the status word
