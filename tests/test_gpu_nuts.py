@@ -314,6 +314,28 @@ def test_nuts_long_signal_streams_match_oracle():
     assert ctx.status() == 0
 
 
+@pytest.mark.parametrize("wname,n,depth", [("bbh11", 300, 6), ("bbh11_long", 64, 4), ("bns", 48, 3)])
+def test_nuts_outputs_equal_likelihood_call(wname, n, depth):
+    """The NUTS kernel evaluates ln L and its gradient with the likelihood's own per-particle phases, sweeps and
+    epilogue (on the long segment, streams shared by the warps of a tick; in the standalone call, the tuner's
+    kernel, the staged one included): the ln L and gradient it returns equal sharpy_loglike_grad at the returned
+    positions bit for bit, on every path and all three segment lengths."""
+    G.require_gpu()
+    w = getattr(inputs, wname)()
+    ctx, th_inj, _ = api.make_event(w, seed=0)
+    th = np.vstack([inputs.prior_draws(w, n // 2, 31), inputs.ball(w, th_inj, n - n // 2, 32, rel=1e-3)])
+    t0 = G.to_dev(th)
+    step = 0.5 * float(np.min(np.std(th, axis=0)))
+    for prec in ("mixed", "split", "fp64"):
+        l0, g0 = ctx.loglike_grad(t0, prec)
+        t, l, g = t0.clone(), l0.clone(), g0.clone()
+        ctx.nuts_mutate(0.3, t, l, g, None, step, depth, 2, key=41, ctr=3, precision=prec)
+        assert not torch.equal(t, t0), prec
+        lc, gc = ctx.loglike_grad(t, prec)
+        assert torch.equal(lc, l) and torch.equal(gc, g), prec
+    assert ctx.status() == 0
+
+
 def test_nuts_slot_count_invariant():
     """The slot count per CTA (sharpy_set_nuts_slots: 4, 8, 16, 32) changes how a CTA schedules its particles'
     sweeps and state machines, never what a particle computes: positions, ln L, gradients and the transition
